@@ -1,0 +1,182 @@
+"""Pins for the oracle's raymarch: phase function, camera rays, slab clipping
+and the integration rules of Sec. 3.1.
+
+* Henyey-Greenstein (Sec. 1): normalisation and mean cosine by quadrature.
+* Homogeneous slab: with density rho0 everywhere, the analytic rule gives
+  RGB = L_in (1 - e^{-rho0 alpha (t1 - t0)}) for EVERY step count and jitter
+  (the step-length independence claimed in Sec. 3.1 / Fig. 2); the basic rule
+  S = T L does not, and converges to it as the step shrinks.
+* Telescoping: with no sun, RGB = A * alpha exactly for any density field.
+* Beer-Lambert (Sec. 1): alpha = 1 - exp(-alpha D sum_i rho_i), independent
+  of the lighting.
+* Convergence: analytic and basic rules approach the same limit as N grows.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1609_05344_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("g", [0.0, 0.3, 0.6, -0.5, 0.85])
+def test_hg_normalised_and_mean_cosine(oracle, g):
+    mu, w = np.polynomial.legendre.leggauss(400)
+    p = np.array([oracle.hg(m, g) for m in mu])
+    assert 2 * math.pi * np.sum(w * p) == pytest.approx(1.0, abs=1e-9)
+    assert 2 * math.pi * np.sum(w * mu * p) == pytest.approx(g, abs=1e-9)
+
+
+def test_hg_isotropic_and_forward_peak(oracle):
+    for m in (-1.0, -0.2, 0.5, 1.0):
+        assert oracle.hg(m, 0.0) == pytest.approx(1.0 / (4 * math.pi), abs=1e-15)
+    assert oracle.hg(1.0, 0.6) > oracle.hg(0.0, 0.6) > oracle.hg(-1.0, 0.6)
+
+
+def test_centre_pixel_is_forward_and_edge_angle(oracle):
+    cam = I.camera((1.0, 2.0, 500.0), 33.0, 20.0, 60.0)
+    d = oracle.pixel_ray(cam, 101, 51, 50, 25)
+    assert np.allclose(d, cam["forward"], atol=1e-15)
+    # top row, centre column: tan(angle to forward) = (1 - 1/H) tan(fovy/2) along up
+    d = oracle.pixel_ray(cam, 101, 51, 50, 0)
+    f, u = np.array(cam["forward"]), np.array(cam["up"])
+    assert np.dot(d, u) / np.dot(d, f) == pytest.approx((1 - 1 / 51) * math.tan(math.radians(30)),
+                                                        rel=1e-13)
+    # rightmost column: aspect ratio applies
+    d = oracle.pixel_ray(cam, 101, 51, 100, 25)
+    r = np.array(cam["right"])
+    assert np.dot(d, r) / np.dot(d, f) == pytest.approx(
+        (1 - 1 / 101) * (101 / 51) * math.tan(math.radians(30)), rel=1e-13)
+    assert np.linalg.norm(d) == pytest.approx(1.0, abs=1e-15)
+
+
+def test_slab_clip_cases(oracle):
+    desc, prm = I.volume_desc("tiny"), I.params()
+    up = np.array([0.0, math.cos(math.radians(30)), math.sin(math.radians(30))])
+    hit, t0, t1 = oracle.slab_clip(desc, prm, (0, 0, 500.0), up)
+    assert hit and t0 == pytest.approx(2000.0) and t1 == pytest.approx(7000.0)
+    hit, _, _ = oracle.slab_clip(desc, prm, (0, 0, 500.0), -up)
+    assert not hit
+    flat = np.array([1.0, 0.0, 0.0])
+    hit, t0, t1 = oracle.slab_clip(desc, prm, (0, 0, 2000.0), flat)
+    assert hit and t0 == 0.0 and t1 == prm["t_max"]
+    hit, _, _ = oracle.slab_clip(desc, prm, (0, 0, 500.0), flat)
+    assert not hit
+    hit, t0, t1 = oracle.slab_clip(desc, prm, (0, 0, 2000.0), up)   # inside the layer
+    assert hit and t0 == 0.0 and t1 == pytest.approx(4000.0)
+    grazing = np.array([math.cos(0.03), 0.0, math.sin(0.03)])      # clipped by t_max
+    hit, t0, t1 = oracle.slab_clip(desc, prm, (0, 0, 500.0), grazing)
+    assert hit and t0 == pytest.approx(1000.0 / math.sin(0.03)) and t1 == prm["t_max"]
+
+
+def _closed_form_pixel(oracle, desc, prm, cam, w, h, x, y, rho0, light_steps):
+    d = oracle.pixel_ray(cam, w, h, x, y)
+    hit, t0, t1 = oracle.slab_clip(desc, prm, cam["pos"], d)
+    if not hit:
+        return np.zeros(4)
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    tau_sun = rho0 * prm["absorption"] * light_steps * prm["light_step"]
+    ph = oracle.hg(float(np.dot(d, s)), prm["hg_g"])
+    l_in = np.array(prm["sun_radiance"]) * math.exp(-tau_sun) * ph + np.array(prm["ambient"])
+    a = -math.expm1(-rho0 * prm["absorption"] * (t1 - t0))
+    return np.concatenate([l_in * a, [a]])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 8, 16, 128])
+@pytest.mark.parametrize("jitter_frame", [-1, 0, 5])
+def test_homogeneous_slab_closed_form(oracle, steps, jitter_frame):
+    rho0 = 0.004
+    desc = I.volume_desc("constant", rho0=rho0)
+    prm = I.params(tau_max=0.0)
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    w, h = 24, 16
+    img, _ = oracle.render(vol, cam, prm, w, h, steps, 6, jitter_frame=jitter_frame)
+    hits = 0
+    for y in range(h):
+        for x in range(w):
+            exp = _closed_form_pixel(oracle, desc, prm, cam, w, h, x, y, rho0, 6)
+            assert np.allclose(img[y, x], exp, atol=1e-12, rtol=0), (x, y)
+            hits += exp[3] > 0
+    assert hits > w * h // 3
+
+
+def test_basic_rule_depends_on_step_length(oracle):
+    rho0 = 0.004
+    desc = I.volume_desc("constant", rho0=rho0)
+    prm = I.params(tau_max=0.0)
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    ref = _closed_form_pixel(oracle, desc, prm, cam, 8, 8, 4, 1, rho0, 6)
+    errs = []
+    for n in (2, 8, 32, 128, 512):
+        img, _ = oracle.render(vol, cam, prm, 8, 8, n, 6, integration=oracle.BASIC)
+        errs.append(np.abs(img[1, 4, :3] - ref[:3]).max())
+    assert errs[0] > 0.05                           # visibly darker with few steps (Fig. 2)
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < errs[0] / 100                 # first-order convergence in the step length
+
+
+@pytest.mark.parametrize("jitter_frame", [-1, 3])
+def test_telescoping_no_sun(oracle, jitter_frame):
+    desc = I.volume_desc("tiny", seed=1)
+    prm = I.params(sun_radiance=(0.0, 0.0, 0.0))
+    vol = oracle.Volume(desc)
+    img, _ = oracle.render(vol, I.ground_camera(), prm, 32, 24, 8, 6, jitter_frame=jitter_frame)
+    amb = np.array(prm["ambient"])
+    assert np.allclose(img[..., :3], img[..., 3:4] * amb, atol=1e-12, rtol=0)
+    assert img[..., 3].max() > 0.5
+
+
+def test_alpha_is_beer_lambert_of_density_sum(oracle):
+    desc = I.volume_desc("tiny", seed=1)
+    prm = I.params(tau_max=0.0)
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    w, h, n = 16, 12, 8
+    img, _ = oracle.render(vol, cam, prm, w, h, n, 6, jitter_frame=2)
+    img2, _ = oracle.render(vol, cam, I.params(tau_max=0.0, sun_radiance=(5, 0, 1), hg_g=-0.2,
+                                               ambient=(0, 1, 0)), w, h, n, 6, jitter_frame=2)
+    assert np.array_equal(img[..., 3], img2[..., 3])
+    for (x, y) in [(3, 2), (8, 6), (15, 11), (0, 0)]:
+        d = oracle.pixel_ray(cam, w, h, x, y)
+        hit, t0, t1 = oracle.slab_clip(desc, prm, cam["pos"], d)
+        if not hit:
+            assert img[y, x, 3] == 0.0
+            continue
+        D = (t1 - t0) / n
+        u = oracle.jitter(desc["seed"], x, y, 2)
+        rho = sum(vol.density(np.array(cam["pos"]) + (t0 + (i + u) * D) * d) for i in range(n))
+        assert img[y, x, 3] == pytest.approx(-math.expm1(-prm["absorption"] * D * rho), abs=1e-13)
+
+
+def test_early_out_bound(oracle):
+    desc = I.volume_desc("tiny", seed=1)
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    a, n_on = oracle.render(vol, cam, I.params(), 32, 32, 64, 6)
+    b, n_off = oracle.render(vol, cam, I.params(tau_max=0.0), 32, 32, 64, 6)
+    assert n_on < n_off
+    # after tau >= 11.5 the rest of the ray carries at most e^-11.5 of the radiance
+    lmax = 2.0 * oracle.hg(1.0, 0.6) + 0.3
+    assert np.abs(a - b).max() <= math.exp(-11.5) * lmax
+
+
+@pytest.mark.slow
+def test_convergence_in_step_count(oracle):
+    desc = I.volume_desc("tiny", seed=1)
+    prm = I.params(tau_max=0.0)
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    w = h = 8
+    ref, _ = oracle.render(vol, cam, prm, w, h, 4096, 6, nthreads=4)
+    basic, _ = oracle.render(vol, cam, prm, w, h, 4096, 6, integration=oracle.BASIC, nthreads=4)
+    errs = []
+    for n in (256, 512, 1024, 2048):
+        img, _ = oracle.render(vol, cam, prm, w, h, n, 6, nthreads=4)
+        errs.append(np.abs(img - ref).max())
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    # the two rules differ by O(D): at N = 4096 they agree closely
+    assert np.abs(basic - ref).max() < 5e-3
+    assert np.abs(basic - ref).max() < np.abs(
+        oracle.render(vol, cam, prm, w, h, 256, 6, integration=oracle.BASIC, nthreads=4)[0] - ref).max()
