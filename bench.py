@@ -1,0 +1,358 @@
+"""Benchmark of the cloud raymarch + TAA frame loop on GB300.
+
+Workload (fast path of the paper, Sec. 3.2 / Sec. 4): 1920x1080, 8 jittered
+view steps x 6 light steps per ray, analytic integration, TAA resolve with
+blend 0.1 over a seeded 32-frame camera orbit; 128^3 base + 32^3 detail noise
+and a 512^2 weather map (FP32 by default, --precision fp16 for half volumes).
+
+One step = one frame: raymarch (jitter frame f) -> reprojection motion ->
+TAA resolve.  Metric: nominal Gsamples/s = W*H*steps*(1+light_steps) / frame
+time, plus ms/frame.  L2 is flushed (256 MiB write) between timed frames,
+outside the timed events.
+
+    python bench.py [--gpus N --steps K --warmup W --precision fp32|fp16]
+    python bench.py --impl reference      # the FP64 CPU oracle on host cores
+
+Multi-GPU (torchrun): every rank renders its own replica of the frame loop
+(independent views; no collective on the data path); value = sum over ranks
+of the samples / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s & ms/frame 1080p 8-step+TAA; served p50/p99 latency; err vs FP64"
+UNIT = "Gsamples/s"
+L1TEX_BYTES_PER_CLK_PER_SM = 128
+FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d.get("hbm_gbs", 6800.0), sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
+        os.environ.get("LOCAL_RANK", 0))
+
+
+def aggregate(step_ms: float, samples: float, world: int, reduce_max=None):
+    """Whole-job throughput: all ranks' samples over the slowest rank's time."""
+    worst = reduce_max(step_ms) if reduce_max else step_ms
+    return samples * world / (worst * 1e-3) / 1e9, worst
+
+
+def cpu_baseline(wl, prm, budget_s=12.0, gpu_frame=None):
+    """The FP64 oracle (test infrastructure) timed on the host cores over whole
+    frames of the workload (render + motion + TAA), as many as fit budget_s."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1609_05344_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    ovol = O.Volume(dict(wl.volume, precision="fp32"))
+    frames, t0 = 0, time.perf_counter()
+    hist, first_img = None, None
+    while True:
+        cam = I.orbit_camera(frames, wl.volume["seed"])
+        img, _ = O.render(ovol, cam, prm, wl.width, wl.height, wl.steps, wl.light_steps,
+                          jitter_frame=frames, nthreads=cores)
+        if first_img is None:
+            first_img = img
+        mot = (O.motion(wl.volume, prm, I.orbit_camera(frames - 1, wl.volume["seed"]), cam,
+                        wl.width, wl.height) if frames else np.zeros((wl.height, wl.width, 2)))
+        hist = O.taa(hist, img, mot, blend=0.1)
+        frames += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    samples = wl.width * wl.height * wl.steps * (1 + wl.light_steps) * frames
+    err = None
+    if gpu_frame is not None:
+        err = float(np.abs(gpu_frame.astype(np.float64) - first_img).max())
+    return {"value": samples / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{frames} whole frame(s) of the workload (render+motion+TAA), FP64, "
+                      f"{cores} threads, {dt:.1f} s"}, err
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (there is no
+    published implementation of the paper to run)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1609_05344_gb300 import inputs as I
+    wl = I.workload("fast-1080p")
+    prm = I.params()
+    cores = os.cpu_count() or 1
+    ovol = O.Volume(wl.volume)
+    band = max(1, wl.height // 16)  # a bounded sample: one 1920x67 band of each frame
+    rows = np.arange(band)
+    xs = np.tile(np.arange(wl.width), band)
+    times = []
+    for f in range(args.warmup + args.steps):
+        cam = I.orbit_camera(f, wl.volume["seed"])
+        y0 = (f * band) % (wl.height - band + 1)
+        ys = np.repeat(rows + y0, wl.width)
+        t0 = time.perf_counter()
+        O.render_pixels(ovol, cam, prm, wl.width, wl.height, wl.steps, wl.light_steps, xs, ys,
+                        jitter_frame=f, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if f >= args.warmup:
+            times.append(dt)
+    per_px = statistics.mean(times) / (band * wl.width)
+    frame_s = per_px * wl.width * wl.height
+    value = wl.width * wl.height * wl.steps * (1 + wl.light_steps) / frame_s / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "fast-1080p", "width": wl.width, "height": wl.height,
+                       "steps": wl.steps, "light_steps": wl.light_steps, "jitter": True,
+                       "taa": True, "volumes": "128^3 base + 32^3 detail + 512^2 weather"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"render of one {wl.width}x{band} band per step, FP64, "
+                                       f"{cores} threads, scaled to a frame"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1609_05344_gb300 import _native, api, inputs as I
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    _native.build()
+
+    wl = I.workload("fast-1080p", precision=args.precision)
+    prm = I.params()
+    W, H, S, LS = wl.width, wl.height, wl.steps, wl.light_steps
+    seed = wl.volume["seed"] + 1000 * rank  # each replica its own orbit start
+    vol = api.Volume(wl.volume)
+    stream = torch.cuda.current_stream()
+    cur = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    mot = torch.zeros((H, W, 2), dtype=torch.float32, device="cuda")
+    hist = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def cam(f):
+        return I.orbit_camera(f % wl.frames, seed)
+
+    state = {"latest": None, "n": 0}
+
+    def frame(f, ev=None):
+        if ev:
+            ev[0].record(stream)
+        api.render(vol, cam(f), prm, W, H, S, LS, jitter_frame=f, out=cur)
+        if ev:
+            ev[1].record(stream)
+        launches = 1
+        src = None
+        if state["latest"] is not None:
+            api.motion(vol, prm, cam(f - 1), cam(f), W, H, out=mot)
+            src = hist[state["latest"]]
+            launches += 1
+        if ev:
+            ev[2].record(stream)
+        nxt = 1 if state["latest"] == 0 else 0
+        api.taa(src, cur, mot, blend=0.1, out=hist[nxt])
+        if ev:
+            ev[3].record(stream)
+        state["latest"] = nxt
+        return launches + 1
+
+    for f in range(args.warmup):
+        frame(f)
+    # effective lookups per frame (untimed counting launches over the timed cameras)
+    counted = []
+    for k in range(min(args.steps, 8)):
+        f = args.warmup + k
+        _, ctr = api.render(vol, cam(f), prm, W, H, S, LS, jitter_frame=f, out=cur, count=True)
+        counted.append(int(ctr.item()))
+    eff_lookups = statistics.mean(counted)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # evict L2 (outside the timed events)
+            launches += frame(args.warmup + k, evs[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    march_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    motion_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    taa_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    ms = statistics.mean(step_ms)
+
+    def reduce_max(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    samples = W * H * S * (1 + LS)
+    value, worst = aggregate(ms, samples, world, reduce_max)
+
+    # end to end through the session API: host pinned output, D2H inside the step
+    host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+    sess = api.Session(vol, W, H, "fp32")
+    for f in range(args.warmup):
+        sess.frame(cam(f), prm, S, LS, host_out=host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        sess.frame(cam(args.warmup + k), prm, S, LS, host_out=host)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_value, _ = aggregate(e2e_s * 1e3, samples, world, reduce_max)
+    sess.close()
+
+    pk = _peaks()
+    sm_mhz = pk["sm_max_mhz"]
+    l1_peak_gbs = 152 * L1TEX_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
+    texel_b = 4 if args.precision == "fp32" else 2
+    bytes_per_lookup = 20 * texel_b  # 8 base + 8 detail + 4 weather texels
+    march_avg = statistics.mean(march_ms)
+    achieved = eff_lookups * bytes_per_lookup / (march_avg * 1e-3) / 1e9
+    taa_avg = statistics.mean(taa_ms)
+    taa_gbs = W * H * 56 / (taa_avg * 1e-3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": worst, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "fast-1080p", "width": W, "height": H, "steps": S,
+                   "light_steps": LS, "jitter": True, "taa": True, "blend": 0.1,
+                   "volume_precision": args.precision,
+                   "volumes": "128^3 base + 32^3 detail + 512^2 weather",
+                   "frames": "32-frame seeded orbit", "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "ms_per_frame": worst, "march_ms": march_avg, "motion_ms": statistics.mean(motion_ms),
+        "taa_ms": taa_avg, "wall_ms_per_step_incl_flush": t_wall / args.steps * 1e3,
+        "effective_lookups_per_frame": eff_lookups,
+        "effective_gsamples_s": eff_lookups / (ms * 1e-3) / 1e9,
+        "roofline": {"bound": "l1tex", "achieved": achieved, "peak": l1_peak_gbs, "unit": "GB/s",
+                     "frac": achieved / l1_peak_gbs, "traffic": None, "kernel": "march_kernel",
+                     "peak_source": f"152 SMs x 128 B/clk x {sm_mhz:.0f} MHz ({pk['source']} clock)",
+                     "algorithmic_bytes_per_lookup": bytes_per_lookup},
+        "taa_roofline": {"bound": "hbm", "achieved": taa_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": taa_gbs / pk["hbm_gbs"], "bytes_per_pixel": 56,
+                         "peak_source": pk["source"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": 216, "d2h_bytes_per_step": W * H * 16},
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        gpu0 = api.render(vol, I.orbit_camera(0, wl.volume["seed"]), prm, W, H, S, LS,
+                          jitter_frame=0).cpu().numpy()
+        base, err = cpu_baseline(wl, prm, gpu_frame=gpu0)
+        line["cpu_baseline"] = base
+        line["max_abs_err_vs_fp64"] = err
+    print(json.dumps(line))
+    vol.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * cloudvol.h -- C ABI of libcloudvol.so, a GB300 (sm_103a) implementation of
+ * the volumetric-cloud raymarch and temporal anti-aliasing resolve of Toft,
+ * Bowles and Zimmermann, "Optimisations for Real-Time Volumetric
+ * Cloudscapes" (arXiv 1609.05344).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status: CLOUD_OK (0) or a negative CLOUD_ERR_*
+ *    code.  No call aborts, traps or exits; cloud_last_error_message() gives
+ *    a one-line description of the last failure on the calling thread.
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device; "host" pointers are ordinary CPU memory.  Buffers passed in are
+ *    owned by the caller unless a call says otherwise.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that take a stream only enqueue work on it and return
+ *    without waiting, unless stated otherwise.
+ *  - Images are row-major, row y = 0 at the top, pixel (x, y) at index
+ *    y * width + x.  RGBA images are 4 floats per pixel, premultiplied by
+ *    alpha.  Motion fields are 2 floats per pixel, in pixels.
+ *  - Cameras are pinholes in a right-handed world with z up, metres.
+ */
+#ifndef CLOUDVOL_H
+#define CLOUDVOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CLOUD_OK 0
+#define CLOUD_ERR_INVALID_ARG (-1)   /* a size, pointer, alignment or enum is invalid */
+#define CLOUD_ERR_OUT_OF_MEMORY (-2) /* a device or host allocation failed           */
+#define CLOUD_ERR_CUDA (-3)          /* the CUDA runtime reported an error           */
+#define CLOUD_ERR_TIMEOUT (-4)       /* a bounded device wait gave up                */
+#define CLOUD_ERR_UNSUPPORTED (-5)   /* valid request this build does not provide    */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define CLOUD_PRECISION_FP32 0 /* volume texels stored as float                  */
+#define CLOUD_PRECISION_FP16 1 /* volume texels stored as IEEE half              */
+#define CLOUD_PRECISION_BF16 2 /* volume texels stored as bfloat16               */
+
+#define CLOUD_DENSITY_NOISE 0    /* fBm base - detail, coverage remap, weather    */
+#define CLOUD_DENSITY_CONSTANT 1 /* constant density everywhere (closed forms)   */
+
+#define CLOUD_INTEGRATE_ANALYTIC 0 /* Sec. 3.1 analytic step integral            */
+#define CLOUD_INTEGRATE_BASIC 1    /* Sec. 3.1 basic S = T L                     */
+
+#define CLOUD_HISTORY_FP32 0 /* TAA history: 4 x float per pixel (16 B)          */
+#define CLOUD_HISTORY_FP16 1 /* TAA history: 4 x IEEE half per pixel (8 B)       */
+
+#define CLOUD_MAX_LIGHT_STEPS 32
+#define CLOUD_MAX_STEPS 4096
+#define CLOUD_MAX_DIM 16384
+
+/* ---- descriptors ------------------------------------------------------- */
+
+/* Cloud density volume.  The paper samples "the density" of a cloud volume
+ * at every step (Sec. 1) without defining it; the field is value-noise fBm:
+ *   rho(p) = g(z) * W(x, y) * max(0, (B(p) - detail_weight * Dt(p) - coverage)
+ *                                      / (1 - coverage))
+ * B: base_n^3 fBm tile spanning base_period_m; Dt: detail_n^3 tile (0 = none,
+ * then Dt = 0); W: weather_n^2 map (0 = none, then W = 1); g: piecewise-linear
+ * height profile over [slab_lo_m, slab_hi_m] (0 outside).  Lattice edges are
+ * powers of two in [16, 1024] (weather up to 4096).  Noise lattice values come
+ * from the counter-based hash keyed by `seed`. */
+typedef struct {
+    uint32_t seed;
+    int32_t base_n;
+    int32_t detail_n;
+    int32_t weather_n;
+    double detail_weight;
+    double base_period_m;
+    double detail_period_m;
+    double weather_period_m;
+    double coverage;         /* in [0, 1)                                      */
+    double slab_lo_m;
+    double slab_hi_m;        /* > slab_lo_m                                    */
+    int32_t density_mode;    /* CLOUD_DENSITY_*                                */
+    double constant_density; /* rho for CLOUD_DENSITY_CONSTANT                 */
+    int32_t precision;       /* CLOUD_PRECISION_*                              */
+} cloud_volume_desc;
+
+/* Pinhole camera: forward/right/up orthonormal; vertical field of view
+ * 2 atan(tan_half_fovy); the horizontal one follows from width/height. */
+typedef struct {
+    double pos[3];
+    double forward[3];
+    double right[3];
+    double up[3];
+    double tan_half_fovy;
+} cloud_camera;
+
+/* Lighting and march constants (Sec. 1): sun direction (towards the sun,
+ * any length, z > 0), sun colour x intensity, ambient radiance, the
+ * Henyey-Greenstein asymmetry g in (-1, 1), absorption alpha per metre at
+ * density 1, light-march step length, early-out optical depth (<= 0 turns the
+ * early out off) and far clip of a view ray. */
+typedef struct {
+    double sun_dir[3];
+    double sun_radiance[3];
+    double ambient[3];
+    double hg_g;
+    double absorption_per_m;
+    double light_step_m;
+    double tau_max;
+    double t_max_m;
+} cloud_params;
+
+typedef struct cloud_volume cloud_volume;   /* opaque, immutable once created */
+typedef struct cloud_session cloud_session; /* opaque, one TAA stream of frames */
+
+/* ---- status ------------------------------------------------------------ */
+const char *cloud_status_string(int status);
+/* Last failure on the calling thread ("" if none). */
+const char *cloud_last_error_message(void);
+
+/* ---- volumes ----------------------------------------------------------- */
+
+/* Creates the density volume described by *desc on the current device and
+ * generates its noise tiles on `stream` (Sec. 1 "density is sampled"; field
+ * as in cloud_volume_desc).  The library allocates and owns the device
+ * memory; the handle may be shared read-only by any number of streams once
+ * `stream` has passed the generation work.  *out is set only on success. */
+int cloud_volume_create(const cloud_volume_desc *desc, void *stream, cloud_volume **out);
+
+/* Frees a volume.  The caller guarantees that no enqueued work still uses it. */
+int cloud_volume_destroy(cloud_volume *vol);
+
+/* Copies the noise tiles into caller-owned device buffers as float values
+ * in [0, 1) (decoding reduced-precision storage): base base_n^3, detail
+ * detail_n^3, weather weather_n^2, x fastest.  Any pointer may be NULL to
+ * skip that tile.  For tests and tools. */
+int cloud_volume_export(const cloud_volume *vol, float *base, float *detail, float *weather,
+                        void *stream);
+
+/* ---- render (Sec. 1, Sec. 3.1, Sec. 3.2) -------------------------------- */
+
+/* Raymarches every pixel of a width x height image into out_rgba (device,
+ * width*height*4 floats, 16-byte aligned, caller-owned):
+ *   steps view samples per ray over the ray's span [t0, t1] inside the
+ *   cloud layer (D = (t1 - t0)/steps, sample i at t0 + (i + u) D);
+ *   u = 1/2, or for jitter_frame >= 0 a per-pixel per-frame value from the
+ *   hash of (x, y, jitter_frame, seed) (Sec. 3.2);
+ *   light_steps samples towards the sun per view sample with density > 0,
+ *   giving L_in = E_sun e^{-tau_sun} p_HG(d.s) + ambient (Sec. 1);
+ *   integration CLOUD_INTEGRATE_ANALYTIC adds e^{-tau} L_in (1 - e^{-sigma D})
+ *   per step, CLOUD_INTEGRATE_BASIC the step-dependent S = T L form
+ *   (Sec. 3.1), sigma = absorption * rho, tau the optical-depth sum;
+ *   the ray stops after the step at which tau >= tau_max (Sec. 1);
+ *   out = (C.rgb, 1 - e^{-tau}).  Rays that miss the layer write 0.
+ * Limits: 1 <= steps <= CLOUD_MAX_STEPS, 0 <= light_steps <=
+ * CLOUD_MAX_LIGHT_STEPS, 1 <= width, height <= CLOUD_MAX_DIM. */
+int cloud_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
+                 int width, int height, int steps, int light_steps, int jitter_frame,
+                 int integration, float *out_rgba, void *stream);
+
+/* As cloud_render, and also adds the number of density evaluations the
+ * launch performed to *lookups (device, one uint64, caller-owned; the caller
+ * zeroes it).  Measures the effective work of a frame. */
+int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
+                       int width, int height, int steps, int light_steps, int jitter_frame,
+                       int integration, float *out_rgba, unsigned long long *lookups,
+                       void *stream);
+
+/* ---- motion and TAA (Sec. 3.2) ----------------------------------------- */
+
+/* Screen-space motion (device, width*height*2 floats, 8-byte aligned) of
+ * each pixel of camera `cur` relative to camera `prev`: the pixel's ray
+ * entry point into the cloud layer (or the point at t_max for rays that do
+ * not enter it ahead of the camera) is projected into `prev`;
+ * motion = pixel centre - that projection.  Points behind `prev` get 1e9. */
+int cloud_motion(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
+                 const cloud_camera *cur, int width, int height, float *motion, void *stream);
+
+/* Temporal anti-aliasing resolve (Sec. 3.2, Playdead-style):
+ *   q = pixel centre - motion; if history == NULL or q is outside
+ *   [0, width] x [0, height]: out = current; otherwise
+ *   h = bilinear sample of history at q (clamp to edge),
+ *   hc = clamp(h, min, max of the 3x3 neighbourhood of current),
+ *   out = hc + blend (current - hc).
+ * history / history_out: device, width*height*4 values of history_fmt,
+ * 16-byte (FP32) or 8-byte (FP16) aligned; they must not overlap.
+ * current: device RGBA float (16-byte aligned); motion: device float2. */
+int taa_resolve(const void *history, const float *current, const float *motion,
+                void *history_out, int width, int height, int history_fmt, float blend,
+                void *stream);
+
+/* ---- sessions: one camera's stream of TAA frames ------------------------- */
+
+/* A session owns the device buffers of one view (current frame, motion,
+ * two history buffers of history_fmt) and its frame index, which is the
+ * jitter frame of Sec. 3.2.  The library allocates and owns the memory. */
+int cloud_session_create(const cloud_volume *vol, int width, int height, int history_fmt,
+                         cloud_session **out);
+int cloud_session_destroy(cloud_session *s);
+
+/* One frame: render with jitter_frame = the session's frame index, motion
+ * from the previous frame's camera, TAA resolve into the other history
+ * buffer, advance the index.  If host_out is not NULL the resolved frame
+ * (width*height*4 values of the history format) is copied to it and the
+ * call waits for the stream; otherwise it returns after enqueueing.
+ * *dev_out (if not NULL) receives the device address of the resolved frame,
+ * valid until the next call on this session. */
+int cloud_session_frame(cloud_session *s, const cloud_camera *cam, const cloud_params *prm,
+                        int steps, int light_steps, int integration, float blend,
+                        void *host_out, const void **dev_out, void *stream);
+
+/* Forgets the history: the next frame is a first frame (index kept). */
+int cloud_session_reset(cloud_session *s);
+
+/* ---- test hooks -------------------------------------------------------- */
+
+/* out[i] = hash(keys[4i], keys[4i+1], keys[4i+2], keys[4i+3]) on the device
+ * (the counter-based hash of the jitter and the noise lattice).  keys and
+ * out are device buffers of 4n and n uint32. */
+int cloud_hash4_batch(const uint32_t *keys, int64_t n, uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLOUDVOL_H */

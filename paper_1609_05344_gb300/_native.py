@@ -1,0 +1,173 @@
+"""Build and load libcloudvol.so, and mirror its C ABI (include/cloudvol.h)
+with ctypes.  Argument marshalling only: every computation runs in the CUDA
+kernels of the library.  There is no fallback: if the library is missing or
+fails to load, the calls raise.
+"""
+from __future__ import annotations
+
+import concurrent.futures
+import ctypes
+import os
+import subprocess
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+CSRC = os.path.join(_HERE, "csrc")
+BUILD_DIR = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_HERE, "libcloudvol.so")
+HEADER = os.path.join(_ROOT, "include", "cloudvol.h")
+SOURCES = ["volume.cu", "render.cu", "taa.cu", "session.cu"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC", "-Xptxas", "-v",
+              "--expt-relaxed-constexpr"]
+
+# status codes and enumerations (include/cloudvol.h)
+OK = 0
+ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
+DENSITY = {"noise": 0, "constant": 1}
+INTEGRATION = {"analytic": 0, "basic": 1}
+HISTORY = {"fp32": 0, "fp16": 1}
+MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM = 32, 4096, 16384
+
+
+def _nvcc() -> str:
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (in parallel) and link the library."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "common.cuh"), HEADER]
+    newest = max(os.path.getmtime(p) for p in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+    objs = []
+
+    def compile_one(src):
+        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+        return obj, r.stderr
+
+    with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
+        for obj, log in ex.map(compile_one, SOURCES):
+            objs.append(obj)
+            if verbose:
+                print(log)
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [nvcc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+           "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class VolumeDesc(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint32), ("base_n", ctypes.c_int32), ("detail_n", ctypes.c_int32),
+                ("weather_n", ctypes.c_int32), ("detail_weight", ctypes.c_double),
+                ("base_period_m", ctypes.c_double), ("detail_period_m", ctypes.c_double),
+                ("weather_period_m", ctypes.c_double), ("coverage", ctypes.c_double),
+                ("slab_lo_m", ctypes.c_double), ("slab_hi_m", ctypes.c_double),
+                ("density_mode", ctypes.c_int32), ("constant_density", ctypes.c_double),
+                ("precision", ctypes.c_int32)]
+
+
+_D3 = ctypes.c_double * 3
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("pos", _D3), ("forward", _D3), ("right", _D3), ("up", _D3),
+                ("tan_half_fovy", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("sun_dir", _D3), ("sun_radiance", _D3), ("ambient", _D3), ("hg_g", ctypes.c_double),
+                ("absorption_per_m", ctypes.c_double), ("light_step_m", ctypes.c_double),
+                ("tau_max", ctypes.c_double), ("t_max_m", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_P = ctypes.POINTER
+
+# (name, restype, argtypes) for every entry point declared in include/cloudvol.h
+SIGNATURES = [
+    ("cloud_status_string", ctypes.c_char_p, [_i]),
+    ("cloud_last_error_message", ctypes.c_char_p, []),
+    ("cloud_volume_create", _i, [_P(VolumeDesc), _vp, _P(_vp)]),
+    ("cloud_volume_destroy", _i, [_vp]),
+    ("cloud_volume_export", _i, [_vp, _vp, _vp, _vp, _vp]),
+    ("cloud_render", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    ("cloud_render_count", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    ("cloud_motion", _i, [_vp, _P(Params), _P(Camera), _P(Camera), _i, _i, _vp, _vp]),
+    ("taa_resolve", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _vp]),
+    ("cloud_session_create", _i, [_vp, _i, _i, _i, _P(_vp)]),
+    ("cloud_session_destroy", _i, [_vp]),
+    ("cloud_session_frame", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, ctypes.c_float, _vp,
+                                 _P(_vp), _vp]),
+    ("cloud_session_reset", _i, [_vp]),
+    ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+        return h
+
+
+class CloudError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        l = lib()
+        msg = l.cloud_last_error_message().decode() or l.cloud_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != OK:
+        raise CloudError(status, where)
+
+
+def volume_desc(d: dict) -> VolumeDesc:
+    return VolumeDesc(int(d.get("seed", 0)) & 0xFFFFFFFF, int(d.get("base_n", 0)),
+                      int(d.get("detail_n", 0)), int(d.get("weather_n", 0)),
+                      float(d.get("detail_weight", 0.0)), float(d.get("base_period", 6400.0)),
+                      float(d.get("detail_period", 800.0)), float(d.get("weather_period", 40000.0)),
+                      float(d.get("coverage", 0.5)), float(d.get("slab_lo", 1500.0)),
+                      float(d.get("slab_hi", 4000.0)), DENSITY[d.get("density_mode", "noise")],
+                      float(d.get("constant_density", 0.0)), PRECISION[d.get("precision", "fp32")])
+
+
+def camera(c: dict) -> Camera:
+    return Camera(_D3(*c["pos"]), _D3(*c["forward"]), _D3(*c["right"]), _D3(*c["up"]),
+                  float(c["tan_half_fovy"]))
+
+
+def params(p: dict) -> Params:
+    return Params(_D3(*p["sun_dir"]), _D3(*p["sun_radiance"]), _D3(*p["ambient"]), float(p["hg_g"]),
+                  float(p["absorption"]), float(p["light_step"]), float(p["tau_max"]),
+                  float(p["t_max"]))

@@ -1,0 +1,186 @@
+"""Python binding of libcloudvol.so (include/cloudvol.h).
+
+PyTorch supplies device memory and streams; every computation runs in the
+library's CUDA kernels.  Inputs are the plain dictionaries produced by
+``inputs.py`` (volume descriptors, cameras, lighting constants).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as N
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=None):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+
+
+class Volume:
+    """A cloud density volume generated on the device (cloud_volume_create)."""
+
+    def __init__(self, desc: dict, stream=None):
+        self.desc = dict(desc)
+        self._h = ctypes.c_void_p()
+        d = N.volume_desc(desc)
+        N.check(N.lib().cloud_volume_create(ctypes.byref(d), _stream(stream), ctypes.byref(self._h)),
+                "cloud_volume_create")
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise RuntimeError("volume destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            torch.cuda.synchronize()
+            N.check(N.lib().cloud_volume_destroy(self._h), "cloud_volume_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, stream=None) -> dict:
+        """Noise tiles as float32 CUDA tensors in [0, 1), indexed [z, y, x] / [y, x]."""
+        d = self.desc
+        out = {}
+        if d.get("density_mode", "noise") == "noise":
+            n = d["base_n"]
+            out["base"] = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+            if d.get("detail_n"):
+                m = d["detail_n"]
+                out["detail"] = torch.empty((m, m, m), dtype=torch.float32, device="cuda")
+            if d.get("weather_n"):
+                m = d["weather_n"]
+                out["weather"] = torch.empty((m, m), dtype=torch.float32, device="cuda")
+        N.check(N.lib().cloud_volume_export(self.handle, _ptr(out.get("base")),
+                                            _ptr(out.get("detail")), _ptr(out.get("weather")),
+                                            _stream(stream)), "cloud_volume_export")
+        return out
+
+
+def render(vol: Volume, cam: dict, prm: dict, width: int, height: int, steps: int,
+           light_steps: int, jitter_frame: int = -1, integration: str = "analytic", out=None,
+           count: bool = False, stream=None):
+    """Raymarch one image (cloud_render).  Returns an (H, W, 4) float32 CUDA
+    tensor of premultiplied RGBA; with count=True also the number of density
+    lookups the launch executed (a 1-element int64 CUDA tensor)."""
+    if out is None:
+        out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
+    _require_cuda(out, "out", torch.float32)
+    if out.numel() != width * height * 4:
+        raise ValueError("out has the wrong size")
+    c, p = N.camera(cam), N.params(prm)
+    if count:
+        ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+        N.check(N.lib().cloud_render_count(vol.handle, ctypes.byref(c), ctypes.byref(p), width,
+                                           height, steps, light_steps, jitter_frame,
+                                           N.INTEGRATION[integration], _ptr(out), _ptr(ctr),
+                                           _stream(stream)), "cloud_render_count")
+        return out, ctr
+    N.check(N.lib().cloud_render(vol.handle, ctypes.byref(c), ctypes.byref(p), width, height, steps,
+                                 light_steps, jitter_frame, N.INTEGRATION[integration], _ptr(out),
+                                 _stream(stream)), "cloud_render")
+    return out
+
+
+def motion(vol: Volume, prm: dict, prev: dict, cur: dict, width: int, height: int, out=None,
+           stream=None):
+    """Per-pixel reprojection motion (cloud_motion): (H, W, 2) float32."""
+    if out is None:
+        out = torch.empty((height, width, 2), dtype=torch.float32, device="cuda")
+    _require_cuda(out, "out", torch.float32)
+    a, b, p = N.camera(prev), N.camera(cur), N.params(prm)
+    N.check(N.lib().cloud_motion(vol.handle, ctypes.byref(p), ctypes.byref(a), ctypes.byref(b),
+                                 width, height, _ptr(out), _stream(stream)), "cloud_motion")
+    return out
+
+
+def taa(history, current: torch.Tensor, motion_px: torch.Tensor, blend: float = 0.1, out=None,
+        history_fmt: str = "fp32", stream=None):
+    """TAA resolve (taa_resolve).  history None means the first frame.
+    history/out are float32 (H, W, 4) or float16 (H, W, 4) per history_fmt."""
+    h, w = current.shape[:2]
+    dt = torch.float32 if history_fmt == "fp32" else torch.float16
+    if out is None:
+        out = torch.empty((h, w, 4), dtype=dt, device="cuda")
+    _require_cuda(current, "current", torch.float32)
+    _require_cuda(motion_px, "motion", torch.float32)
+    _require_cuda(out, "out", dt)
+    if history is not None:
+        _require_cuda(history, "history", dt)
+    N.check(N.lib().taa_resolve(_ptr(history), _ptr(current), _ptr(motion_px), _ptr(out), w, h,
+                                N.HISTORY[history_fmt], float(blend), _stream(stream)),
+            "taa_resolve")
+    return out
+
+
+class Session:
+    """One camera's stream of jittered frames resolved by TAA (cloud_session_*)."""
+
+    def __init__(self, vol: Volume, width: int, height: int, history_fmt: str = "fp32"):
+        self.vol, self.width, self.height, self.history_fmt = vol, width, height, history_fmt
+        self._h = ctypes.c_void_p()
+        N.check(N.lib().cloud_session_create(vol.handle, width, height, N.HISTORY[history_fmt],
+                                             ctypes.byref(self._h)), "cloud_session_create")
+
+    def close(self):
+        if self._h:
+            torch.cuda.synchronize()
+            N.check(N.lib().cloud_session_destroy(self._h), "cloud_session_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        N.check(N.lib().cloud_session_reset(self._h), "cloud_session_reset")
+
+    def frame(self, cam: dict, prm: dict, steps: int, light_steps: int, blend: float = 0.1,
+              integration: str = "analytic", host_out=None, stream=None):
+        """Render + motion + resolve one frame.  With host_out (a pinned CPU
+        tensor of H*W*4 elements) the resolved frame is copied there and the
+        call waits; otherwise returns a CUDA tensor view of the resolved frame
+        (valid until the next frame)."""
+        c, p = N.camera(cam), N.params(prm)
+        dev = ctypes.c_void_p()
+        hp = ctypes.c_void_p(host_out.data_ptr()) if host_out is not None else ctypes.c_void_p()
+        N.check(N.lib().cloud_session_frame(self._h, ctypes.byref(c), ctypes.byref(p), steps,
+                                            light_steps, N.INTEGRATION[integration], float(blend),
+                                            hp, ctypes.byref(dev), _stream(stream)),
+                "cloud_session_frame")
+        if host_out is not None:
+            return host_out
+        return dev.value
+
+
+def hash4(keys: torch.Tensor, stream=None) -> torch.Tensor:
+    """Device hash of (n, 4) int32/uint32 keys (cloud_hash4_batch) -> (n,) int32 bits."""
+    _require_cuda(keys, "keys")
+    if keys.element_size() != 4 or keys.shape[-1] != 4:
+        raise ValueError("keys must be (n, 4) 32-bit")
+    n = keys.numel() // 4
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    N.check(N.lib().cloud_hash4_batch(_ptr(keys), n, _ptr(out), _stream(stream)),
+            "cloud_hash4_batch")
+    return out

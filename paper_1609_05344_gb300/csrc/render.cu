@@ -1,0 +1,378 @@
+// render.cu -- the per-pixel cloud raymarch (Sec. 1, Sec. 3.1, Sec. 3.2).
+//
+// One thread per pixel; a 128-thread CTA covers a 16x8 pixel tile and each
+// warp an 8x4 sub-tile, so the rays of a warp stay adjacent and touch the
+// same region of the (L2-resident) noise tiles.
+//
+// Precision design.  Grazing rays are tens of kilometres long and, with 8
+// view steps, a step is kilometres long; the estimator then multiplies any
+// density error by alpha*D*L_in (hundreds), so sample positions must be far
+// more accurate than FP32 world coordinates allow.  Per ray, the start and
+// the step of every lattice axis (base xyz, detail xyz, weather xy) and of the
+// height above the layer bottom are computed in FP64 and stored as 32-bit
+// fixed-point values.  A lattice axis keeps log2(N) integer bits and
+// 32-log2(N) fraction bits, so unsigned overflow is exactly the periodic wrap
+// of the tile; a view step adds the ray's increment and a light sample adds a
+// per-launch constant offset -- integer adds, no rounding.  The texel index is
+// the top log2(N) bits, the interpolation weight the next 23 bits.  Radiance
+// and the optical-depth sum are FP32.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace cloudvol {
+
+enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
+
+struct MarchParams {
+    // camera: unnormalised ray v(x, y) = v00 + x vx + y vy; origin o
+    double v00[3], vx[3], vy[3], o[3];
+    double slab_lo, slab_hi, t_max;
+    // fixed-point coordinate of lattice axis a at ray distance t:
+    //   afix[a] + t * d[comp[a]] * kfix[a]   (mod 2^32)
+    double afix[kLatticeAxes], kfix[kLatticeAxes];
+    // height above the layer bottom, in 2^-16 m: hfix0 + t * d_z * 65536
+    double hfix0;
+    uint32_t loff[CLOUD_MAX_LIGHT_STEPS][kLatticeAxes];  // light-sample offsets
+    int32_t lh[CLOUD_MAX_LIGHT_STEPS];                   // light-sample height offsets
+    int32_t h_top;                                       // layer thickness in 2^-16 m
+    float h_lo_scale, h_hi_scale;  // 10/thickness, 2.5/thickness, per 2^-16 m
+    float sun[3], sun_rad[3], ambient[3];
+    float hg_g, absorption, light_step, tau_max;
+    float k0, b_cut, inv_1mc, detail_w, rho0;
+    int log2_base, log2_detail, log2_weather;
+    int width, height, steps, light_steps, jitter_frame, integration, constant_mode;
+    uint32_t jitter_key;
+};
+
+__device__ __forceinline__ float frac23(uint32_t f) {
+    return __uint_as_float((f >> 9) | 0x3F800000u) - 1.0f;
+}
+
+// Trilinear sample of a 2^L cube at fixed-point coordinates (wrap by masking).
+template <typename T>
+__device__ __forceinline__ float sample3(const T *__restrict__ tex, int L, uint32_t cx, uint32_t cy,
+                                         uint32_t cz) {
+    const int sh = 32 - L;
+    const uint32_t mask = (1u << L) - 1u;
+    const uint32_t x0 = cx >> sh, y0 = cy >> sh, z0 = cz >> sh;
+    const uint32_t x1 = (x0 + 1u) & mask, y1 = (y0 + 1u) & mask, z1 = (z0 + 1u) & mask;
+    const float fx = frac23(cx << L), fy = frac23(cy << L), fz = frac23(cz << L);
+    const uint32_t r00 = (z0 << (2 * L)) | (y0 << L), r01 = (z0 << (2 * L)) | (y1 << L);
+    const uint32_t r10 = (z1 << (2 * L)) | (y0 << L), r11 = (z1 << (2 * L)) | (y1 << L);
+    const float a00 = load_texel(tex, r00 | x0), b00 = load_texel(tex, r00 | x1);
+    const float a01 = load_texel(tex, r01 | x0), b01 = load_texel(tex, r01 | x1);
+    const float a10 = load_texel(tex, r10 | x0), b10 = load_texel(tex, r10 | x1);
+    const float a11 = load_texel(tex, r11 | x0), b11 = load_texel(tex, r11 | x1);
+    const float c00 = fmaf(fx, b00 - a00, a00), c01 = fmaf(fx, b01 - a01, a01);
+    const float c10 = fmaf(fx, b10 - a10, a10), c11 = fmaf(fx, b11 - a11, a11);
+    const float c0 = fmaf(fy, c01 - c00, c00), c1 = fmaf(fy, c11 - c10, c10);
+    return fmaf(fz, c1 - c0, c0);
+}
+
+template <typename T>
+__device__ __forceinline__ float sample2(const T *__restrict__ tex, int L, uint32_t cx, uint32_t cy) {
+    const int sh = 32 - L;
+    const uint32_t mask = (1u << L) - 1u;
+    const uint32_t x0 = cx >> sh, y0 = cy >> sh;
+    const uint32_t x1 = (x0 + 1u) & mask, y1 = (y0 + 1u) & mask;
+    const float fx = frac23(cx << L), fy = frac23(cy << L);
+    const float a0 = load_texel(tex, (y0 << L) | x0), b0 = load_texel(tex, (y0 << L) | x1);
+    const float a1 = load_texel(tex, (y1 << L) | x0), b1 = load_texel(tex, (y1 << L) | x1);
+    const float c0 = fmaf(fx, b0 - a0, a0), c1 = fmaf(fx, b1 - a1, a1);
+    return fmaf(fy, c1 - c0, c0);
+}
+
+// Density at a sample (Sec. 1 "the density is sampled"):
+//   rho = g(h) W max(0, (B - w_d Dt - c)/(1 - c)),
+// tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0.
+// Terms that cannot change a zero result are skipped (g = 0, W = 0, B <= c).
+template <typename T>
+__device__ __forceinline__ float density(const MarchParams &p, const T *__restrict__ base,
+                                         const T *__restrict__ detail,
+                                         const T *__restrict__ weather, const uint32_t c[8],
+                                         int32_t hq) {
+    if (p.constant_mode) return p.rho0;
+    const float ga = fminf(fmaxf((float)hq * p.h_lo_scale, 0.0f), 1.0f);
+    const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
+    const float g = ga * gb;
+    if (g <= 0.0f) return 0.0f;
+    float w = 1.0f;
+    if (weather) {
+        w = sample2(weather, p.log2_weather, c[kWX], c[kWY]) + kCentre;
+        if (w <= 0.0f) return 0.0f;
+    }
+    const float b = sample3(base, p.log2_base, c[kBX], c[kBY], c[kBZ]);
+    float r;
+    if (detail) {
+        if (b + p.b_cut <= 0.0f) return 0.0f;  // B <= c: detail cannot raise it
+        const float dt = sample3(detail, p.log2_detail, c[kDX], c[kDY], c[kDZ]);
+        r = fmaf(-p.detail_w, dt, b + p.k0);
+    } else {
+        r = b + p.k0;
+    }
+    r = fmaxf(r * p.inv_1mc, 0.0f);
+    return g * w * r;
+}
+
+__device__ __forceinline__ uint32_t to_fixed(double v) {
+    return (uint32_t)(unsigned long long)__double2ll_rn(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p,
+                                                    const T *__restrict__ base,
+                                                    const T *__restrict__ detail,
+                                                    const T *__restrict__ weather,
+                                                    float4 *__restrict__ out,
+                                                    unsigned long long *__restrict__ counter) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    unsigned long long n_look = 0;
+    if (x < p.width && y < p.height) {
+        // --- a1: pixel ray and layer clip (FP64) -----------------------------
+        const double vxw = fma((double)y, p.vy[0], fma((double)x, p.vx[0], p.v00[0]));
+        const double vyw = fma((double)y, p.vy[1], fma((double)x, p.vx[1], p.v00[1]));
+        const double vzw = fma((double)y, p.vy[2], fma((double)x, p.vx[2], p.v00[2]));
+        const double rn = rsqrt(vxw * vxw + vyw * vyw + vzw * vzw);
+        const double d0 = vxw * rn, d1 = vyw * rn, d2 = vzw * rn;
+        double t0, t1;
+        bool hit;
+        if (fabs(d2) < 1e-8) {
+            hit = p.o[2] >= p.slab_lo && p.o[2] <= p.slab_hi;
+            t0 = 0.0;
+            t1 = p.t_max;
+        } else {
+            const double inv = 1.0 / d2;
+            const double tl = (p.slab_lo - p.o[2]) * inv, th = (p.slab_hi - p.o[2]) * inv;
+            t0 = fmax(fmin(tl, th), 0.0);
+            t1 = fmin(fmax(tl, th), p.t_max);
+            hit = t1 > t0;
+        }
+        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (hit) {
+            // --- a2: jittered start offset (Sec. 3.2) ---------------------------
+            const double D = (t1 - t0) / (double)p.steps;
+            double u = 0.5;
+            if (p.jitter_frame >= 0)
+                u = (double)(pcg_hash4((uint32_t)x, (uint32_t)y, (uint32_t)p.jitter_frame,
+                                       p.jitter_key) >> 8) * (1.0 / 16777216.0);
+            const double ts = fma(u, D, t0);
+            const double dc[3] = {d0, d1, d2};
+            uint32_t c[kLatticeAxes], e[kLatticeAxes];
+#pragma unroll
+            for (int a = 0; a < kLatticeAxes; ++a) {
+                const double kd = dc[a < 6 ? a % 3 : a - 6] * p.kfix[a];
+                c[a] = to_fixed(fma(ts, kd, p.afix[a]));
+                e[a] = to_fixed(D * kd);
+            }
+            const double kh = d2 * 65536.0;
+            int32_t hq = (int32_t)__double2ll_rn(fma(ts, kh, p.hfix0));
+            const int32_t eh = (int32_t)__double2ll_rn(D * kh);
+            const float Df = (float)D;
+            // --- a5: phase, hoisted per ray ------------------------------------
+            const float mu = (float)(d0 * p.sun[0] + d1 * p.sun[1] + d2 * p.sun[2]);
+            const float g = p.hg_g;
+            const float den = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
+            const float phase = (1.0f - g * g) / (4.0f * 3.14159265358979f * den * sqrtf(den));
+            float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+            for (int i = 0; i < p.steps; ++i) {
+                // --- a3: density lookup ---------------------------------------
+                const float rho = density(p, base, detail, weather, c, hq);
+                ++n_look;
+                if (rho > 0.0f) {
+                    // --- a4: light march towards the sun (Sec. 1) ----------------
+                    float rho_sum = 0.0f;
+                    for (int j = 0; j < p.light_steps; ++j) {
+                        uint32_t cj[kLatticeAxes];
+#pragma unroll
+                        for (int a = 0; a < kLatticeAxes; ++a) cj[a] = c[a] + p.loff[j][a];
+                        rho_sum += density(p, base, detail, weather, cj, hq + p.lh[j]);
+                    }
+                    n_look += p.light_steps;
+                    // --- a5: in-scattered light ---------------------------------
+                    const float sun_t = expf(-p.absorption * p.light_step * rho_sum) * phase;
+                    const float lr = fmaf(p.sun_rad[0], sun_t, p.ambient[0]);
+                    const float lg = fmaf(p.sun_rad[1], sun_t, p.ambient[1]);
+                    const float lb = fmaf(p.sun_rad[2], sun_t, p.ambient[2]);
+                    // --- a6: per-step integral (Sec. 3.1) ----------------------
+                    const float sd = p.absorption * rho * Df;
+                    float wgt;
+                    if (p.integration == CLOUD_INTEGRATE_ANALYTIC) {
+                        wgt = expf(-tau) * -expm1f(-sd);
+                        tau += sd;
+                    } else {
+                        tau += sd;
+                        wgt = expf(-tau) * sd;
+                    }
+                    cr = fmaf(wgt, lr, cr);
+                    cg = fmaf(wgt, lg, cg);
+                    cb = fmaf(wgt, lb, cb);
+                }
+                // --- a7: early out once alpha is ~1 (Sec. 1) --------------------
+                if (tau >= p.tau_max) break;
+#pragma unroll
+                for (int a = 0; a < kLatticeAxes; ++a) c[a] += e[a];
+                hq += eh;
+            }
+            res = make_float4(cr, cg, cb, -expm1f(-tau));
+        }
+        // --- a8: premultiplied RGBA, one 16-byte store -------------------------
+        out[(size_t)y * p.width + x] = res;
+    }
+    if (counter) {
+        unsigned long long v = n_look;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, s);
+        if (lane == 0 && v) atomicAdd(counter, v);
+    }
+}
+
+double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
+                 int width, int height, int steps, int light_steps, int jitter_frame,
+                 int integration, MarchParams *p) {
+    if (width < 1 || height < 1 || width > CLOUD_MAX_DIM || height > CLOUD_MAX_DIM)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: width/height outside [1, 16384]");
+    if (steps < 1 || steps > CLOUD_MAX_STEPS)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: steps outside [1, 4096]");
+    if (light_steps < 0 || light_steps > CLOUD_MAX_LIGHT_STEPS)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: light_steps outside [0, 32]");
+    if (integration != CLOUD_INTEGRATE_ANALYTIC && integration != CLOUD_INTEGRATE_BASIC)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad integration mode");
+    if (!(cam->tan_half_fovy > 0.0) || !(prm->t_max_m > 0.0) || !(prm->light_step_m >= 0.0) ||
+        !(prm->absorption_per_m >= 0.0) || !(prm->hg_g > -1.0 && prm->hg_g < 1.0))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad camera or lighting constants");
+    const double sn = std::sqrt(dot3(prm->sun_dir, prm->sun_dir));
+    if (!(sn > 0.0) || !(prm->sun_dir[2] > 0.0))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: sun direction must have z > 0");
+    const cloud_volume_desc &d = vol->desc;
+    const double thick = d.slab_hi_m - d.slab_lo_m;
+    const double s[3] = {prm->sun_dir[0] / sn, prm->sun_dir[1] / sn, prm->sun_dir[2] / sn};
+    if (thick + light_steps * prm->light_step_m * s[2] > 32000.0)
+        return set_error(CLOUD_ERR_UNSUPPORTED, "cloud_render: light march reaches > 32 km above the layer bottom");
+
+    *p = MarchParams{};
+    const double aspect = (double)width / (double)height, tf = cam->tan_half_fovy;
+    const double a0 = (1.0 / width - 1.0) * aspect * tf, ax = 2.0 * aspect * tf / width;
+    const double b0 = (1.0 - 1.0 / height) * tf, by = -2.0 * tf / height;
+    for (int k = 0; k < 3; ++k) {
+        p->v00[k] = cam->forward[k] + a0 * cam->right[k] + b0 * cam->up[k];
+        p->vx[k] = ax * cam->right[k];
+        p->vy[k] = by * cam->up[k];
+        p->o[k] = cam->pos[k];
+    }
+    p->slab_lo = d.slab_lo_m;
+    p->slab_hi = d.slab_hi_m;
+    p->t_max = prm->t_max_m;
+    const bool noise = d.density_mode == CLOUD_DENSITY_NOISE;
+    const int L[kLatticeAxes] = {vol->log2_base,   vol->log2_base,   vol->log2_base,
+                                 vol->log2_detail, vol->log2_detail, vol->log2_detail,
+                                 vol->log2_weather, vol->log2_weather};
+    const double P[kLatticeAxes] = {d.base_period_m,   d.base_period_m,   d.base_period_m,
+                                    d.detail_period_m, d.detail_period_m, d.detail_period_m,
+                                    d.weather_period_m, d.weather_period_m};
+    for (int a = 0; a < kLatticeAxes; ++a) {
+        const int comp = a < 6 ? a % 3 : a - 6;
+        if (!noise || L[a] == 0) continue;  // absent tile: axis unused
+        const double unit = std::ldexp(1.0, 32 - L[a]);  // fixed-point units per texel
+        p->kfix[a] = (double)(1 << L[a]) / P[a] * unit;
+        p->afix[a] = cam->pos[comp] * p->kfix[a] - 0.5 * unit;
+        for (int j = 0; j < light_steps; ++j) {
+            const double v = (j + 0.5) * prm->light_step_m * s[comp] * p->kfix[a];
+            p->loff[j][a] = (uint32_t)(unsigned long long)std::llrint(v);
+        }
+    }
+    p->hfix0 = (cam->pos[2] - d.slab_lo_m) * 65536.0;
+    for (int j = 0; j < light_steps; ++j)
+        p->lh[j] = (int32_t)std::llrint((j + 0.5) * prm->light_step_m * s[2] * 65536.0);
+    p->h_top = (int32_t)std::llrint(thick * 65536.0);
+    p->h_lo_scale = (float)(10.0 / (thick * 65536.0));
+    p->h_hi_scale = (float)(2.5 / (thick * 65536.0));
+    for (int k = 0; k < 3; ++k) {
+        p->sun[k] = (float)s[k];
+        p->sun_rad[k] = (float)prm->sun_radiance[k];
+        p->ambient[k] = (float)prm->ambient[k];
+    }
+    p->hg_g = (float)prm->hg_g;
+    p->absorption = (float)prm->absorption_per_m;
+    p->light_step = (float)prm->light_step_m;
+    p->tau_max = prm->tau_max > 0.0 ? (float)prm->tau_max : INFINITY;
+    const double wd = vol->log2_detail ? d.detail_weight : 0.0;
+    p->detail_w = (float)wd;
+    p->k0 = (float)(0.5 - d.coverage - 0.5 * wd);
+    p->b_cut = (float)(0.5 - d.coverage);
+    p->inv_1mc = (float)(1.0 / (1.0 - d.coverage));
+    p->rho0 = (float)d.constant_density;
+    p->log2_base = vol->log2_base;
+    p->log2_detail = vol->log2_detail;
+    p->log2_weather = vol->log2_weather;
+    p->width = width;
+    p->height = height;
+    p->steps = steps;
+    p->light_steps = light_steps;
+    p->jitter_frame = jitter_frame < 0 ? -1 : jitter_frame;
+    p->integration = integration;
+    p->constant_mode = noise ? 0 : 1;
+    p->jitter_key = d.seed ^ kJitterKey;
+    return CLOUD_OK;
+}
+
+int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
+                  int width, int height, int steps, int light_steps, int jitter_frame,
+                  int integration, float *out, unsigned long long *counter, cudaStream_t s) {
+    if (!vol || !cam || !prm || !out)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: null pointer");
+    if (!aligned(out, 16)) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: out_rgba not 16-byte aligned");
+    if (counter && !aligned(counter, 8))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: counter not 8-byte aligned");
+    MarchParams p;
+    if (int rc = build_params(vol, cam, prm, width, height, steps, light_steps, jitter_frame,
+                              integration, &p))
+        return rc;
+    const dim3 grid((width + 15) / 16, (height + 7) / 8);
+    switch (vol->desc.precision) {
+        case CLOUD_PRECISION_FP32:
+            march_kernel<float><<<grid, 128, 0, s>>>(p, (const float *)vol->base,
+                                                     (const float *)vol->detail,
+                                                     (const float *)vol->weather, (float4 *)out,
+                                                     counter);
+            break;
+        case CLOUD_PRECISION_FP16:
+            march_kernel<__half><<<grid, 128, 0, s>>>(p, (const __half *)vol->base,
+                                                      (const __half *)vol->detail,
+                                                      (const __half *)vol->weather, (float4 *)out,
+                                                      counter);
+            break;
+        default:
+            march_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(
+                p, (const __nv_bfloat16 *)vol->base, (const __nv_bfloat16 *)vol->detail,
+                (const __nv_bfloat16 *)vol->weather, (float4 *)out, counter);
+    }
+    return check_launch("march_kernel");
+}
+
+}  // namespace cloudvol
+
+using namespace cloudvol;
+
+extern "C" int cloud_render(const cloud_volume *vol, const cloud_camera *cam,
+                            const cloud_params *prm, int width, int height, int steps,
+                            int light_steps, int jitter_frame, int integration, float *out_rgba,
+                            void *stream) {
+    clear_error();
+    return launch_render(vol, cam, prm, width, height, steps, light_steps, jitter_frame,
+                         integration, out_rgba, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam,
+                                  const cloud_params *prm, int width, int height, int steps,
+                                  int light_steps, int jitter_frame, int integration,
+                                  float *out_rgba, unsigned long long *lookups, void *stream) {
+    clear_error();
+    if (!lookups) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render_count: null counter");
+    return launch_render(vol, cam, prm, width, height, steps, light_steps, jitter_frame,
+                         integration, out_rgba, lookups, (cudaStream_t)stream);
+}

@@ -1,0 +1,210 @@
+"""GPU parity of the raymarch (cloud_render) against the FP64 oracle.
+
+Tolerances (max-abs RGBA): 1e-4 for FP32 volumes, 3e-3 for FP16 volumes;
+the closed-form and telescoping identities to 2e-5 / 2e-6.  Small cases are
+compared on every pixel (sizes with ragged tails over several 16x8 tiles);
+the full-size workloads are compared on seeded pixel samples the oracle
+evaluates one by one, from a full-size launch."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1609_05344_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-4
+TOL_FP16 = 3e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_05344_gb300 import _native, api as A
+    _native.build()
+    return A
+
+
+def _max_err(a, b):
+    return float(np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)).max())
+
+
+def test_hash_bitwise(api, oracle):
+    import torch
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 1 << 32, (1 << 20, 4), dtype=np.uint64).astype(np.uint32)
+    keys[:1024, :] = np.arange(4096, dtype=np.uint32).reshape(1024, 4)  # structured keys too
+    got = api.hash4(torch.from_numpy(keys.view(np.int32)).cuda()).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, oracle.hash4_batch(keys))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-7), ("fp16", 2.5e-4), ("bf16", 2e-3)])
+def test_volume_generation(api, oracle, precision, tol):
+    desc = I.volume_desc("full", seed=2, precision=precision, base_n=64)
+    tiles = api.Volume(desc).export()
+    ov = oracle.Volume(desc)
+    assert _max_err(tiles["base"].cpu().numpy(), ov.base) <= tol
+    assert _max_err(tiles["detail"].cpu().numpy(), ov.detail) <= tol
+    assert _max_err(tiles["weather"].cpu().numpy(), ov.weather) <= tol
+
+
+@pytest.mark.parametrize("w,h", [(128, 128), (37, 23), (1, 1), (200, 9)])
+def test_plain_tiny_full_image(api, oracle, w, h):
+    wl = I.workload("plain-tiny")
+    vol, ovol = api.Volume(wl.volume), oracle.Volume(wl.volume)
+    cam = I.ground_camera()
+    if (w, h) == (1, 1):
+        cam = I.camera((0.0, 0.0, 500.0), 0.0, 45.0, 60.0)  # the single ray hits the layer
+    got = api.render(vol, cam, I.params(), w, h, wl.steps, wl.light_steps).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, I.params(), w, h, wl.steps, wl.light_steps, nthreads=8)
+    assert _max_err(got, ref) <= TOL_FP32
+    assert ref[..., 3].max() > 0.1
+
+
+@pytest.mark.parametrize("frame", [0, 5, 31])
+@pytest.mark.parametrize("integration", ["analytic", "basic"])
+def test_full_volume_jittered_small(api, oracle, frame, integration):
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    cam = I.orbit_camera(frame, 3)
+    w, h = 96, 54
+    got = api.render(vol, cam, I.params(), w, h, 8, 6, jitter_frame=frame,
+                     integration=integration).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, I.params(), w, h, 8, 6, jitter_frame=frame,
+                           integration=1 if integration == "basic" else 0, nthreads=8)
+    assert _max_err(got, ref) <= TOL_FP32
+
+
+def _sampled(api, oracle, wl, cam, frame, n, seed, precision="fp32", steps=None):
+    desc = dict(wl.volume, precision=precision)
+    vol = api.Volume(desc)
+    ovol = oracle.Volume(dict(wl.volume, precision="fp32"))
+    steps = steps or wl.steps
+    img = api.render(vol, cam, I.params(), wl.width, wl.height, steps, wl.light_steps,
+                     jitter_frame=frame).cpu().numpy()
+    rng = np.random.default_rng(seed)
+    xs = rng.integers(0, wl.width, n)
+    ys = rng.integers(0, wl.height, n)
+    # the last row/column and the four corners are always checked
+    xs = np.concatenate([xs, [0, wl.width - 1, 0, wl.width - 1], rng.integers(0, wl.width, 16),
+                         np.full(16, wl.width - 1)])
+    ys = np.concatenate([ys, [0, 0, wl.height - 1, wl.height - 1], np.full(16, wl.height - 1),
+                         rng.integers(0, wl.height, 16)])
+    ref, _ = oracle.render_pixels(ovol, cam, I.params(), wl.width, wl.height, steps,
+                                  wl.light_steps, xs, ys, jitter_frame=frame, nthreads=8)
+    return _max_err(img[ys, xs], ref), img
+
+
+@pytest.mark.parametrize("frame", [0, 7, 19])
+def test_fast_1080p_sampled(api, oracle, frame):
+    wl = I.workload("fast-1080p")
+    err, img = _sampled(api, oracle, wl, I.orbit_camera(frame, 3), frame, 60000, 100 + frame)
+    assert err <= TOL_FP32
+    assert np.isfinite(img).all()
+
+
+def test_fast_1080p_fp16_volumes(api, oracle):
+    wl = I.workload("fast-1080p")
+    err, _ = _sampled(api, oracle, wl, I.orbit_camera(3, 3), 3, 40000, 5, precision="fp16")
+    assert err <= TOL_FP16
+
+
+def test_reference_720p_sampled(api, oracle):
+    wl = I.workload("reference")
+    err, _ = _sampled(api, oracle, wl, I.ground_camera(), -1, 4000, 9)
+    assert err <= TOL_FP32
+
+
+def _closed_form(oracle, desc, prm, cam, w, h, rho0, ls):
+    out = np.zeros((h, w, 4))
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    for y in range(h):
+        for x in range(w):
+            d = oracle.pixel_ray(cam, w, h, x, y)
+            hit, t0, t1 = oracle.slab_clip(desc, prm, cam["pos"], d)
+            if not hit:
+                continue
+            ph = oracle.hg(float(np.dot(d, s)), prm["hg_g"])
+            lin = (np.array(prm["sun_radiance"]) * math.exp(-rho0 * prm["absorption"] * ls *
+                                                            prm["light_step"]) * ph
+                   + np.array(prm["ambient"]))
+            a = -math.expm1(-rho0 * prm["absorption"] * (t1 - t0))
+            out[y, x, :3], out[y, x, 3] = lin * a, a
+    return out
+
+
+@pytest.mark.parametrize("steps", [1, 3, 8, 128])
+def test_homogeneous_slab_closed_form_on_gpu(api, oracle, steps):
+    rho0 = 0.004
+    desc = I.volume_desc("constant", rho0=rho0)
+    prm = I.params(tau_max=0.0)
+    cam = I.ground_camera()
+    w, h = 40, 24
+    got = api.render(api.Volume(desc), cam, prm, w, h, steps, 6, jitter_frame=2).cpu().numpy()
+    assert _max_err(got, _closed_form(oracle, desc, prm, cam, w, h, rho0, 6)) <= 2e-5
+
+
+def test_telescoping_no_sun_on_gpu(api):
+    desc = I.volume_desc("full", seed=3)
+    prm = I.params(sun_radiance=(0.0, 0.0, 0.0))
+    got = api.render(api.Volume(desc), I.orbit_camera(0, 3), prm, 160, 90, 8, 6,
+                     jitter_frame=4).cpu().numpy().astype(np.float64)
+    amb = np.array(prm["ambient"])
+    assert _max_err(got[..., :3], got[..., 3:4] * amb) <= 2e-6
+    assert got[..., 3].max() > 0.5
+
+
+@pytest.mark.parametrize("case", ["inside-layer", "looking-down", "no-light-steps", "one-step",
+                                  "no-early-out", "horizontal"])
+def test_edge_cases(api, oracle, case):
+    desc = I.volume_desc("full", seed=5)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    prm = I.params()
+    cam = I.ground_camera()
+    steps, ls = 8, 6
+    if case == "inside-layer":
+        cam = I.camera((100.0, 200.0, 2600.0), 40.0, 5.0, 60.0)
+    elif case == "looking-down":
+        cam = I.camera((0.0, 0.0, 500.0), 0.0, -60.0, 40.0)
+    elif case == "no-light-steps":
+        ls = 0
+    elif case == "one-step":
+        steps = 1
+    elif case == "no-early-out":
+        prm = I.params(tau_max=0.0)
+    elif case == "horizontal":
+        cam = I.camera((0.0, 0.0, 2000.0), 10.0, 0.0, 50.0)
+    w, h = 33, 17
+    got = api.render(vol, cam, prm, w, h, steps, ls, jitter_frame=1).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, prm, w, h, steps, ls, jitter_frame=1, nthreads=8)
+    assert _max_err(got, ref) <= TOL_FP32
+    if case == "looking-down":
+        assert np.all(got == 0.0)
+
+
+def test_lookup_count_matches_oracle(api, oracle):
+    wl = I.workload("plain-tiny")
+    vol, ovol = api.Volume(wl.volume), oracle.Volume(wl.volume)
+    cam = I.ground_camera()
+    _, ctr = api.render(vol, cam, I.params(), 64, 48, 16, 6, count=True)
+    _, n = oracle.render(ovol, cam, I.params(), 64, 48, 16, 6)
+    # the two sides may disagree on a handful of near-threshold rho > 0 / early-out decisions
+    assert abs(int(ctr.item()) - n) <= 0.001 * n
+
+
+def test_invalid_arguments_raise(api):
+    import torch
+    from paper_1609_05344_gb300._native import CloudError
+    vol = api.Volume(I.volume_desc("tiny"))
+    out = torch.empty((8, 8, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(CloudError):
+        api.render(vol, I.ground_camera(), I.params(), 8, 8, 0, 6, out=out)
+    with pytest.raises(CloudError):
+        api.render(vol, I.ground_camera(), I.params(), 8, 8, 8, 33, out=out)
+    with pytest.raises(CloudError):
+        api.render(vol, I.ground_camera(), I.params(sun_dir=(0.0, 1.0, -0.2)), 8, 8, 8, 6, out=out)
+    with pytest.raises(CloudError):
+        api.Volume(I.volume_desc("tiny", base_n=100))

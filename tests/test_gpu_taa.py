@@ -1,0 +1,95 @@
+"""GPU parity of motion (cloud_motion), the TAA resolve (taa_resolve) and the
+session frame loop against the FP64 oracle.
+
+The resolve is compared on identical seeded synthetic inputs (history,
+current frame, motion with off-screen pixels); each side takes the same
+off-screen and bilinear-weight decisions exactly, so FP32 history agrees to
+rounding (1e-6) and FP16 history to its storage rounding (2e-3 for values up
+to 2).  The frame loop runs each side's own chain (render -> motion -> TAA)
+over an orbit and compares at the FP32 tolerance 1e-4."""
+import numpy as np
+import pytest
+
+from paper_1609_05344_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_05344_gb300 import _native, api as A
+    _native.build()
+    return A
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("w,h", [(160, 90), (37, 23), (1920, 1080)])
+def test_motion_parity(api, oracle, w, h):
+    desc = I.volume_desc("full", seed=3)
+    vol = api.Volume(desc)
+    prm = I.params()
+    for f in (1, 9):
+        prev, cur = I.orbit_camera(f - 1, 3), I.orbit_camera(f, 3)
+        got = api.motion(vol, prm, prev, cur, w, h).cpu().numpy()
+        ref = oracle.motion(desc, prm, prev, cur, w, h)
+        assert np.abs(got - ref).max() <= 1e-4
+    # a camera turned away: every point is behind the previous camera
+    prev = I.camera((0.0, 0.0, 500.0), 180.0, 20.0, 60.0)
+    cur = I.camera((0.0, 0.0, 500.0), 0.0, 20.0, 60.0)
+    got = api.motion(vol, prm, prev, cur, 16, 8).cpu().numpy()
+    assert np.all(got == np.float32(1e9))
+
+
+@pytest.mark.parametrize("w,h", [(64, 48), (33, 17), (1, 1), (1920, 1080)])
+@pytest.mark.parametrize("fmt", ["fp32", "fp16"])
+def test_taa_parity_synthetic(api, oracle, w, h, fmt):
+    rng = np.random.default_rng(w * 7 + h)
+    hist = I.synthetic_frame(rng, h, w)
+    cur = I.synthetic_frame(rng, h, w)
+    mot = I.synthetic_motion(rng, h, w)
+    hist_in = hist.astype(np.float16) if fmt == "fp16" else hist
+    got = api.taa(_t(hist_in), _t(cur), _t(mot), blend=0.1, history_fmt=fmt).cpu().numpy()
+    ref = oracle.taa(hist_in.astype(np.float64), cur.astype(np.float64), mot.astype(np.float64))
+    tol = 1e-6 if fmt == "fp32" else 2e-3
+    assert np.abs(got.astype(np.float64) - ref).max() <= tol
+    first = api.taa(None, _t(cur), _t(mot), history_fmt=fmt).cpu().numpy()
+    assert np.abs(first.astype(np.float64) - cur).max() <= (0 if fmt == "fp32" else 2e-3)
+
+
+def test_taa_rejects_overlap(api):
+    import torch
+    from paper_1609_05344_gb300._native import CloudError
+    buf = torch.zeros((8, 8, 4), dtype=torch.float32, device="cuda")
+    mot = torch.zeros((8, 8, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(CloudError):
+        api.taa(buf, buf, mot, out=buf)
+
+
+@pytest.mark.parametrize("fmt,tol", [("fp32", 1e-4), ("fp16", 3e-3)])
+def test_session_matches_oracle_chain(api, oracle, fmt, tol):
+    import torch
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    prm = I.params()
+    w, h, frames = 120, 68, 8
+    sess = api.Session(vol, w, h, history_fmt=fmt)
+    host = torch.empty((h, w, 4), dtype=torch.float32 if fmt == "fp32" else torch.float16,
+                       pin_memory=True)
+    ohist = None
+    for f in range(frames):
+        cam = I.orbit_camera(f, 3)
+        sess.frame(cam, prm, 8, 6, blend=0.1, host_out=host)
+        ocur, _ = oracle.render(ovol, cam, prm, w, h, 8, 6, jitter_frame=f, nthreads=8)
+        omot = (oracle.motion(desc, prm, I.orbit_camera(f - 1, 3), cam, w, h) if f
+                else np.zeros((h, w, 2)))
+        ohist = oracle.taa(ohist, ocur, omot, blend=0.1)
+        err = np.abs(host.numpy().astype(np.float64) - ohist).max()
+        assert err <= tol, (f, err)
+    sess.close()
