@@ -41,6 +41,7 @@ extern "C" {
 #define CLOUD_PRECISION_FP32 0 /* volume texels stored as float                  */
 #define CLOUD_PRECISION_FP16 1 /* volume texels stored as IEEE half              */
 #define CLOUD_PRECISION_BF16 2 /* volume texels stored as bfloat16               */
+#define CLOUD_PRECISION_UNORM16 3 /* texels as 16-bit fixed point v * 65536      */
 
 #define CLOUD_DENSITY_NOISE 0    /* fBm base - detail, coverage remap, weather    */
 #define CLOUD_DENSITY_CONSTANT 1 /* constant density everywhere (closed forms)   */

@@ -25,7 +25,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC", "-X
 # status codes and enumerations (include/cloudvol.h)
 OK = 0
 ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
-PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
+PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "unorm16": 3}
 DENSITY = {"noise": 0, "constant": 1}
 INTEGRATION = {"analytic": 0, "basic": 1}
 HISTORY = {"fp32": 0, "fp16": 1}

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 
 #include "../../include/cloudvol.h"
@@ -74,6 +75,83 @@ inline int ilog2(int n) {
 
 inline size_t precision_bytes(int p) { return p == CLOUD_PRECISION_FP32 ? 4 : 2; }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, about
+// 48 significant bits from FP32 operations only (error-free transformations
+// of Knuth/Dekker: two-sum, fast-two-sum, FMA-based two-product).  Used where
+// a per-ray quantity needs more than FP32 precision; GB300's FP64 rate is far
+// below its FP32 rate.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // requires |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+    const float p = a.hi * b;
+    const float e = fmaf(a.hi, b, -p);
+    return fast_two_sum(p, fmaf(a.lo, b, e));
+}
+// 1/b: one Newton step on the FP32 reciprocal.
+__device__ __forceinline__ df df_recip(df b) {
+    const float q = 1.0f / b.hi;
+    const df p = df_mulf(b, q);                 // b q = 1 - r
+    const float r = (1.0f - p.hi) - p.lo;
+    return fast_two_sum(q, q * r);
+}
+// 1/sqrt(a): one Newton step on the FP32 estimate.
+__device__ __forceinline__ df df_rsqrt(df a) {
+    const float r = rsqrtf(a.hi);
+    const df t = df_mulf(df_mulf(a, r), r);     // a r^2 = 1 - e
+    const float e = (1.0f - t.hi) - t.lo;
+    return fast_two_sum(r, 0.5f * r * e);
+}
+__device__ __forceinline__ bool df_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ df df_max(df a, df b) { return df_gt(a, b) ? a : b; }
+__device__ __forceinline__ df df_min(df a, df b) { return df_gt(a, b) ? b : a; }
+// round(a) modulo 2^32 (fixed-point wrap); |a| < 2^62.
+__device__ __forceinline__ uint32_t df_to_u32(df a) {
+    const long long h = __float2ll_rn(a.hi);
+    const float rem = (a.hi - (float)h) + a.lo;
+    return (uint32_t)h + (uint32_t)__float2int_rn(rem);
+}
+
+// Host: split an FP64 value into a double-float pair.
+inline void split_df(double v, float *hi, float *lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+}
+// Host: split so that x * hi is exact in FP32 for integer |x| < 2^14 (hi keeps
+// 10 significant bits) and lo carries the rest.
+inline void split_df10(double v, float *hi, float *lo) {
+    if (v == 0.0) {
+        *hi = *lo = 0.0f;
+        return;
+    }
+    int e;
+    std::frexp(v, &e);
+    const double q = std::ldexp(1.0, e - 10);
+    *hi = (float)(std::nearbyint(v / q) * q);
+    *lo = (float)(v - (double)*hi);
+}
+
 // Texel loads through the read-only path, decoded to float.
 __device__ __forceinline__ float load_texel(const float *p, uint32_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_texel(const __half *p, uint32_t i) {
@@ -81,6 +159,11 @@ __device__ __forceinline__ float load_texel(const __half *p, uint32_t i) {
 }
 __device__ __forceinline__ float load_texel(const __nv_bfloat16 *p, uint32_t i) {
     return __bfloat162float(__ldg(p + i));
+}
+// 16-bit fixed point q = round(v * 2^16) stores v in [0,1) to 2^-17; the
+// centred value q 2^-16 - 1/2 is built exactly from the float bit pattern.
+__device__ __forceinline__ float load_texel(const uint16_t *p, uint32_t i) {
+    return __uint_as_float(0x3F800000u | ((uint32_t)__ldg(p + i) << 7)) - 1.5f;
 }
 
 }  // namespace cloudvol

@@ -25,14 +25,18 @@ namespace cloudvol {
 enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
 
 struct MarchParams {
-    // camera: unnormalised ray v(x, y) = v00 + x vx + y vy; origin o
-    double v00[3], vx[3], vy[3], o[3];
-    double slab_lo, slab_hi, t_max;
-    // fixed-point coordinate of lattice axis a at ray distance t:
-    //   afix[a] + t * d[comp[a]] * kfix[a]   (mod 2^32)
-    double afix[kLatticeAxes], kfix[kLatticeAxes];
-    // height above the layer bottom, in 2^-16 m: hfix0 + t * d_z * 65536
-    double hfix0;
+    // Camera rays, unnormalised: v(x, y) = v00 + x vx + y vy, as double-float
+    // pairs; vx/vy are split so that x * hi is exact (see split_df10).
+    float v00h[3], v00l[3], vxh[3], vxl[3], vyh[3], vyl[3];
+    float oh[3], ol[3];          // camera position
+    float zlo_h, zlo_l;          // slab_lo - o_z
+    float zhi_h, zhi_l;          // slab_hi - o_z
+    float tmax_h, tmax_l;        // far clip distance
+    float invn_h, invn_l;        // 1 / steps
+    // Fixed-point lattice coordinates: unit 2^32 per tile period, so
+    // coordinate = p * kfix - half_unit (mod 2^32), kfix = 2^32 / period.
+    float kfix_h[kLatticeAxes], kfix_l[kLatticeAxes];
+    uint32_t half_unit[kLatticeAxes];  // half a texel: 2^(31 - log2 N)
     uint32_t loff[CLOUD_MAX_LIGHT_STEPS][kLatticeAxes];  // light-sample offsets
     int32_t lh[CLOUD_MAX_LIGHT_STEPS];                   // light-sample height offsets
     int32_t h_top;                                       // layer thickness in 2^-16 m
@@ -42,6 +46,7 @@ struct MarchParams {
     float k0, b_cut, inv_1mc, detail_w, rho0;
     int log2_base, log2_detail, log2_weather;
     int width, height, steps, light_steps, jitter_frame, integration, constant_mode;
+    int cam_in_layer;
     uint32_t jitter_key;
 };
 
@@ -115,8 +120,9 @@ __device__ __forceinline__ float density(const MarchParams &p, const T *__restri
     return g * w * r;
 }
 
-__device__ __forceinline__ uint32_t to_fixed(double v) {
-    return (uint32_t)(unsigned long long)__double2ll_rn(v);
+__device__ __forceinline__ df df_addf(df a, float b) {
+    const df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
 }
 
 template <typename T>
@@ -131,48 +137,61 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     unsigned long long n_look = 0;
     if (x < p.width && y < p.height) {
-        // --- a1: pixel ray and layer clip (FP64) -----------------------------
-        const double vxw = fma((double)y, p.vy[0], fma((double)x, p.vx[0], p.v00[0]));
-        const double vyw = fma((double)y, p.vy[1], fma((double)x, p.vx[1], p.v00[1]));
-        const double vzw = fma((double)y, p.vy[2], fma((double)x, p.vx[2], p.v00[2]));
-        const double rn = rsqrt(vxw * vxw + vyw * vyw + vzw * vzw);
-        const double d0 = vxw * rn, d1 = vyw * rn, d2 = vzw * rn;
-        double t0, t1;
+        // --- a1: pixel ray and layer clip (double-float) ---------------------
+        // p(lambda) = o + lambda v with v unnormalised; t = lambda |v|.
+        const float xf = (float)x, yf = (float)y;
+        df v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            df a = {p.v00h[k], p.v00l[k] + fmaf(xf, p.vxl[k], yf * p.vyl[k])};
+            a = df_addf(a, xf * p.vxh[k]);  // exact products
+            v[k] = df_addf(a, yf * p.vyh[k]);
+        }
+        const df n2 = df_add(df_add(df_mul(v[0], v[0]), df_mul(v[1], v[1])), df_mul(v[2], v[2]));
+        const df rn = df_rsqrt(n2);  // 1 / |v|
+        const df lam_max = df_mul({p.tmax_h, p.tmax_l}, rn);
+        df lam0 = {0.0f, 0.0f}, lam1 = lam_max;
         bool hit;
-        if (fabs(d2) < 1e-8) {
-            hit = p.o[2] >= p.slab_lo && p.o[2] <= p.slab_hi;
-            t0 = 0.0;
-            t1 = p.t_max;
+        if (fabsf(v[2].hi) * rn.hi < 1e-8f) {
+            hit = p.cam_in_layer != 0;
         } else {
-            const double inv = 1.0 / d2;
-            const double tl = (p.slab_lo - p.o[2]) * inv, th = (p.slab_hi - p.o[2]) * inv;
-            t0 = fmax(fmin(tl, th), 0.0);
-            t1 = fmin(fmax(tl, th), p.t_max);
-            hit = t1 > t0;
+            const df inv = df_recip(v[2]);
+            const df ll = df_mul({p.zlo_h, p.zlo_l}, inv), lh = df_mul({p.zhi_h, p.zhi_l}, inv);
+            lam0 = df_max(df_min(ll, lh), lam0);
+            lam1 = df_min(df_max(ll, lh), lam_max);
+            hit = df_gt(lam1, lam0);
         }
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         if (hit) {
             // --- a2: jittered start offset (Sec. 3.2) ---------------------------
-            const double D = (t1 - t0) / (double)p.steps;
-            double u = 0.5;
+            const df D = df_mul(df_add(lam1, df_neg(lam0)), {p.invn_h, p.invn_l});
+            float u = 0.5f;
             if (p.jitter_frame >= 0)
-                u = (double)(pcg_hash4((uint32_t)x, (uint32_t)y, (uint32_t)p.jitter_frame,
-                                       p.jitter_key) >> 8) * (1.0 / 16777216.0);
-            const double ts = fma(u, D, t0);
-            const double dc[3] = {d0, d1, d2};
+                u = (float)(pcg_hash4((uint32_t)x, (uint32_t)y, (uint32_t)p.jitter_frame,
+                                      p.jitter_key) >> 8) * (1.0f / 16777216.0f);
+            const df lam_s = df_add(lam0, df_mulf(D, u));
+            df pos[3], dpos[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pos[k] = df_add({p.oh[k], p.ol[k]}, df_mul(lam_s, v[k]));
+                dpos[k] = df_mul(D, v[k]);
+            }
             uint32_t c[kLatticeAxes], e[kLatticeAxes];
 #pragma unroll
             for (int a = 0; a < kLatticeAxes; ++a) {
-                const double kd = dc[a < 6 ? a % 3 : a - 6] * p.kfix[a];
-                c[a] = to_fixed(fma(ts, kd, p.afix[a]));
-                e[a] = to_fixed(D * kd);
+                const int comp = a < 6 ? a % 3 : a - 6;
+                const df k = {p.kfix_h[a], p.kfix_l[a]};
+                c[a] = df_to_u32(df_mul(pos[comp], k)) - p.half_unit[a];
+                e[a] = df_to_u32(df_mul(dpos[comp], k));
             }
-            const double kh = d2 * 65536.0;
-            int32_t hq = (int32_t)__double2ll_rn(fma(ts, kh, p.hfix0));
-            const int32_t eh = (int32_t)__double2ll_rn(D * kh);
-            const float Df = (float)D;
+            // height above the layer bottom: (o_z - slab_lo) + lambda v_z, in 2^-16 m
+            const df hrel = df_add(df_mul(lam_s, v[2]), df_neg({p.zlo_h, p.zlo_l}));
+            int32_t hq = (int32_t)df_to_u32({hrel.hi * 65536.0f, hrel.lo * 65536.0f});
+            const int32_t eh = (int32_t)df_to_u32({dpos[2].hi * 65536.0f, dpos[2].lo * 65536.0f});
+            const float vlen = n2.hi * rn.hi;
+            const float Df = D.hi * vlen;
             // --- a5: phase, hoisted per ray ------------------------------------
-            const float mu = (float)(d0 * p.sun[0] + d1 * p.sun[1] + d2 * p.sun[2]);
+            const float mu = (v[0].hi * p.sun[0] + v[1].hi * p.sun[1] + v[2].hi * p.sun[2]) * rn.hi;
             const float g = p.hg_g;
             const float den = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
             const float phase = (1.0f - g * g) / (4.0f * 3.14159265358979f * den * sqrtf(den));
@@ -242,7 +261,8 @@ int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: light_steps outside [0, 32]");
     if (integration != CLOUD_INTEGRATE_ANALYTIC && integration != CLOUD_INTEGRATE_BASIC)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad integration mode");
-    if (!(cam->tan_half_fovy > 0.0) || !(prm->t_max_m > 0.0) || !(prm->light_step_m >= 0.0) ||
+    if (!(cam->tan_half_fovy > 0.0) || !(prm->t_max_m > 0.0 && prm->t_max_m <= 1e6) ||
+        !(prm->light_step_m >= 0.0) ||
         !(prm->absorption_per_m >= 0.0) || !(prm->hg_g > -1.0 && prm->hg_g < 1.0))
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad camera or lighting constants");
     const double sn = std::sqrt(dot3(prm->sun_dir, prm->sun_dir));
@@ -259,14 +279,16 @@ int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
     const double a0 = (1.0 / width - 1.0) * aspect * tf, ax = 2.0 * aspect * tf / width;
     const double b0 = (1.0 - 1.0 / height) * tf, by = -2.0 * tf / height;
     for (int k = 0; k < 3; ++k) {
-        p->v00[k] = cam->forward[k] + a0 * cam->right[k] + b0 * cam->up[k];
-        p->vx[k] = ax * cam->right[k];
-        p->vy[k] = by * cam->up[k];
-        p->o[k] = cam->pos[k];
+        split_df(cam->forward[k] + a0 * cam->right[k] + b0 * cam->up[k], &p->v00h[k], &p->v00l[k]);
+        split_df10(ax * cam->right[k], &p->vxh[k], &p->vxl[k]);
+        split_df10(by * cam->up[k], &p->vyh[k], &p->vyl[k]);
+        split_df(cam->pos[k], &p->oh[k], &p->ol[k]);
     }
-    p->slab_lo = d.slab_lo_m;
-    p->slab_hi = d.slab_hi_m;
-    p->t_max = prm->t_max_m;
+    split_df(d.slab_lo_m - cam->pos[2], &p->zlo_h, &p->zlo_l);
+    split_df(d.slab_hi_m - cam->pos[2], &p->zhi_h, &p->zhi_l);
+    split_df(prm->t_max_m, &p->tmax_h, &p->tmax_l);
+    split_df(1.0 / steps, &p->invn_h, &p->invn_l);
+    p->cam_in_layer = cam->pos[2] >= d.slab_lo_m && cam->pos[2] <= d.slab_hi_m;
     const bool noise = d.density_mode == CLOUD_DENSITY_NOISE;
     const int L[kLatticeAxes] = {vol->log2_base,   vol->log2_base,   vol->log2_base,
                                  vol->log2_detail, vol->log2_detail, vol->log2_detail,
@@ -277,15 +299,14 @@ int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
     for (int a = 0; a < kLatticeAxes; ++a) {
         const int comp = a < 6 ? a % 3 : a - 6;
         if (!noise || L[a] == 0) continue;  // absent tile: axis unused
-        const double unit = std::ldexp(1.0, 32 - L[a]);  // fixed-point units per texel
-        p->kfix[a] = (double)(1 << L[a]) / P[a] * unit;
-        p->afix[a] = cam->pos[comp] * p->kfix[a] - 0.5 * unit;
+        const double kfix = 4294967296.0 / P[a];  // 2^32 fixed-point units per tile
+        split_df(kfix, &p->kfix_h[a], &p->kfix_l[a]);
+        p->half_unit[a] = 1u << (31 - L[a]);
         for (int j = 0; j < light_steps; ++j) {
-            const double v = (j + 0.5) * prm->light_step_m * s[comp] * p->kfix[a];
+            const double v = (j + 0.5) * prm->light_step_m * s[comp] * kfix;
             p->loff[j][a] = (uint32_t)(unsigned long long)std::llrint(v);
         }
     }
-    p->hfix0 = (cam->pos[2] - d.slab_lo_m) * 65536.0;
     for (int j = 0; j < light_steps; ++j)
         p->lh[j] = (int32_t)std::llrint((j + 0.5) * prm->light_step_m * s[2] * 65536.0);
     p->h_top = (int32_t)std::llrint(thick * 65536.0);
@@ -346,10 +367,15 @@ int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_
                                                       (const __half *)vol->weather, (float4 *)out,
                                                       counter);
             break;
-        default:
+        case CLOUD_PRECISION_BF16:
             march_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(
                 p, (const __nv_bfloat16 *)vol->base, (const __nv_bfloat16 *)vol->detail,
                 (const __nv_bfloat16 *)vol->weather, (float4 *)out, counter);
+            break;
+        default:
+            march_kernel<uint16_t><<<grid, 128, 0, s>>>(
+                p, (const uint16_t *)vol->base, (const uint16_t *)vol->detail,
+                (const uint16_t *)vol->weather, (float4 *)out, counter);
     }
     return check_launch("march_kernel");
 }

@@ -11,45 +11,71 @@
 namespace cloudvol {
 
 struct MotionParams {
-    double v00[3], vx[3], vy[3], o[3];  // current camera rays, as in the raymarch
-    double op[3], rp[3], up[3], fp[3];  // previous camera
-    double slab_lo, slab_hi, t_max;
-    double inv_atp, inv_tp;             // 1/(aspect tan) and 1/tan of the previous camera
-    int width, height;
+    // current camera, camera-space ray slopes: a = a0 + x ax, b = b0 + y by;
+    // the ray is (a, b, 1) in (right, up, forward) coordinates
+    float a0, ax, b0, by;
+    float rz, uz, fz;      // world z of the current right, up, forward
+    float zlo, zhi, tmax;  // slab_lo - o_z, slab_hi - o_z, far clip
+    // previous camera: q = dlt + lambda (I + G) (a, b, 1), G = R' R^T - I,
+    // dlt = R' (o - o'); projections compared as differences of slopes
+    float G[3][3], dlt[3];
+    float kx, ky, kx1, ky1;  // aT'/aT, T'/T, and the same minus 1
+    float sx, sy;            // W / (2 aT'), H / (2 T')
+    int width, height, cam_in_layer;
+    // exact (FP64) restatement for near-tie layer-entry decisions
+    double v00[3], vx[3], vy[3], oz, slab_lo, slab_hi, t_max;
 };
 
-// Motion of one pixel (FP64: the reprojection depth reaches 40 km and the
-// result is a difference of nearly equal pixel positions).
+// Reprojection depth parameter lambda (t / |v|) of the layer entry point, or
+// of the far clip when the ray does not enter the layer ahead of the camera.
+__device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, int y, float vlen) {
+    double v[3];
+    for (int k = 0; k < 3; ++k) v[k] = fma((double)y, p.vy[k], fma((double)x, p.vx[k], p.v00[k]));
+    const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double dz = v[2] / n;
+    if (fabs(dz) < 1e-8) return (float)(p.t_max / n);
+    const double tl = (p.slab_lo - p.oz) / dz, th = (p.slab_hi - p.oz) / dz;
+    const double t0 = fmax(fmin(tl, th), 0.0), t1 = fmin(fmax(tl, th), p.t_max);
+    return (float)(((t1 > t0 && t0 > 0.0) ? t0 : p.t_max) / n);
+}
+
+// Motion of one pixel.  The motion is a small difference of nearly equal
+// pixel positions; it is computed directly as a difference of camera-space
+// slopes (no large terms cancel), so FP32 keeps it to ~1e-6 pixel.
 __global__ void __launch_bounds__(256) motion_kernel(const __grid_constant__ MotionParams p,
                                                      float2 *__restrict__ motion) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     if (x >= p.width || y >= p.height) return;
-    double v[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = fma((double)y, p.vy[k], fma((double)x, p.vx[k], p.v00[k]));
-    const double rn = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    const double d[3] = {v[0] * rn, v[1] * rn, v[2] * rn};
-    double t = p.t_max;
-    if (fabs(d[2]) >= 1e-8) {
-        const double inv = 1.0 / d[2];
-        const double tl = (p.slab_lo - p.o[2]) * inv, th = (p.slab_hi - p.o[2]) * inv;
-        const double t0 = fmax(fmin(tl, th), 0.0), t1 = fmin(fmax(tl, th), p.t_max);
-        if (t1 > t0 && t0 > 0.0) t = t0;
+    const float a = fmaf((float)x, p.ax, p.a0), b = fmaf((float)y, p.by, p.b0);
+    const float vlen = sqrtf(fmaf(a, a, fmaf(b, b, 1.0f)));
+    const float vz = fmaf(a, p.rz, fmaf(b, p.uz, p.fz));
+    const float lmax = p.tmax / vlen;
+    float lam = lmax;
+    if (fabsf(vz) >= 1e-8f * vlen) {
+        const float ll = p.zlo / vz, lh = p.zhi / vz;
+        const float l0 = fmaxf(fminf(ll, lh), 0.0f), l1 = fminf(fmaxf(ll, lh), lmax);
+        if (fabsf(l1 - l0) <= 1e-5f * fmaxf(l1, l0))
+            lam = entry_lambda_exact(p, x, y, vlen);  // too close to call in FP32
+        else if (l1 > l0 && l0 > 0.0f)
+            lam = l0;
+    } else if (!p.cam_in_layer) {
+        lam = lmax;
     }
-    double q[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) q[k] = fma(t, d[k], p.o[k] - p.op[k]);
-    const double cx = q[0] * p.rp[0] + q[1] * p.rp[1] + q[2] * p.rp[2];
-    const double cy = q[0] * p.up[0] + q[1] * p.up[1] + q[2] * p.up[2];
-    const double cz = q[0] * p.fp[0] + q[1] * p.fp[1] + q[2] * p.fp[2];
+    const float g0 = fmaf(p.G[0][0], a, fmaf(p.G[0][1], b, p.G[0][2]));
+    const float g1 = fmaf(p.G[1][0], a, fmaf(p.G[1][1], b, p.G[1][2]));
+    const float g2 = fmaf(p.G[2][0], a, fmaf(p.G[2][1], b, p.G[2][2]));
+    const float qz = fmaf(lam, 1.0f + g2, p.dlt[2]);
     float2 m;
-    if (cz <= 0.0) {
+    if (qz <= 0.0f) {
         m = make_float2(1e9f, 1e9f);
     } else {
-        const double icz = 1.0 / cz;
-        const double px = (cx * icz * p.inv_atp + 1.0) * 0.5 * p.width;
-        const double py = (1.0 - cy * icz * p.inv_tp) * 0.5 * p.height;
-        m = make_float2((float)((x + 0.5) - px), (float)((y + 0.5) - py));
+        // a kx qz - qx and qy - b ky qz, expanded so the O(lambda) terms cancel exactly
+        const float nx = fmaf(a * p.kx, p.dlt[2], -p.dlt[0]) +
+                         lam * fmaf(a, p.kx1, fmaf(a * p.kx, g2, -g0));
+        const float ny = fmaf(-b * p.ky, p.dlt[2], p.dlt[1]) +
+                         lam * fmaf(-b, p.ky1, fmaf(-b * p.ky, g2, g1));
+        const float iq = 1.0f / qz;
+        m = make_float2(p.sx * nx * iq, p.sy * ny * iq);
     }
     motion[(size_t)y * p.width + x] = m;
 }
@@ -141,26 +167,53 @@ int build_motion_params(const cloud_volume *vol, const cloud_params *prm, const 
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_motion: width/height outside [1, 16384]");
     if (!(cur->tan_half_fovy > 0.0) || !(prev->tan_half_fovy > 0.0) || !(prm->t_max_m > 0.0))
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_motion: bad camera or t_max");
-    const double aspect = (double)width / (double)height, tf = cur->tan_half_fovy;
-    const double a0 = (1.0 / width - 1.0) * aspect * tf, ax = 2.0 * aspect * tf / width;
-    const double b0 = (1.0 - 1.0 / height) * tf, by = -2.0 * tf / height;
+    *p = MotionParams{};
+    const double aspect = (double)width / (double)height;
+    const double aT = aspect * cur->tan_half_fovy, aTp = aspect * prev->tan_half_fovy;
+    const double T = cur->tan_half_fovy, Tp = prev->tan_half_fovy;
+    p->a0 = (float)((1.0 / width - 1.0) * aT);
+    p->ax = (float)(2.0 * aT / width);
+    p->b0 = (float)((1.0 - 1.0 / height) * T);
+    p->by = (float)(-2.0 * T / height);
+    p->rz = (float)cur->right[2];
+    p->uz = (float)cur->up[2];
+    p->fz = (float)cur->forward[2];
+    p->zlo = (float)(vol->desc.slab_lo_m - cur->pos[2]);
+    p->zhi = (float)(vol->desc.slab_hi_m - cur->pos[2]);
+    p->tmax = (float)prm->t_max_m;
+    // rows of R (current) and R' (previous): right, up, forward
+    const double *R[3] = {cur->right, cur->up, cur->forward};
+    const double *Rp[3] = {prev->right, prev->up, prev->forward};
+    for (int i = 0; i < 3; ++i) {
+        double dl = 0.0;
+        for (int k = 0; k < 3; ++k) dl += Rp[i][k] * (cur->pos[k] - prev->pos[k]);
+        p->dlt[i] = (float)dl;
+        for (int j = 0; j < 3; ++j) {
+            double mij = 0.0;  // (R' R^T)_ij = Rp_i . R_j
+            for (int k = 0; k < 3; ++k) mij += Rp[i][k] * R[j][k];
+            p->G[i][j] = (float)(mij - (i == j ? 1.0 : 0.0));
+        }
+    }
+    p->kx = (float)(aTp / aT);
+    p->ky = (float)(Tp / T);
+    p->kx1 = (float)((aTp - aT) / aT);
+    p->ky1 = (float)((Tp - T) / T);
+    p->sx = (float)(width / (2.0 * aTp));
+    p->sy = (float)(height / (2.0 * Tp));
+    p->width = width;
+    p->height = height;
+    p->cam_in_layer = cur->pos[2] >= vol->desc.slab_lo_m && cur->pos[2] <= vol->desc.slab_hi_m;
+    const double a0 = (1.0 / width - 1.0) * aT, ax = 2.0 * aT / width;
+    const double b0 = (1.0 - 1.0 / height) * T, by = -2.0 * T / height;
     for (int k = 0; k < 3; ++k) {
         p->v00[k] = cur->forward[k] + a0 * cur->right[k] + b0 * cur->up[k];
         p->vx[k] = ax * cur->right[k];
         p->vy[k] = by * cur->up[k];
-        p->o[k] = cur->pos[k];
-        p->op[k] = prev->pos[k];
-        p->rp[k] = prev->right[k];
-        p->up[k] = prev->up[k];
-        p->fp[k] = prev->forward[k];
     }
+    p->oz = cur->pos[2];
     p->slab_lo = vol->desc.slab_lo_m;
     p->slab_hi = vol->desc.slab_hi_m;
     p->t_max = prm->t_max_m;
-    p->inv_atp = 1.0 / (aspect * prev->tan_half_fovy);
-    p->inv_tp = 1.0 / prev->tan_half_fovy;
-    p->width = width;
-    p->height = height;
     return CLOUD_OK;
 }
 

@@ -51,6 +51,12 @@ __device__ __forceinline__ __nv_bfloat16 encode<__nv_bfloat16>(double v) {
     return __double2bfloat16(v);
 }
 
+template <>
+__device__ __forceinline__ uint16_t encode<uint16_t>(double v) {
+    const double q = rint((v + (double)kCentre) * 65536.0);
+    return (uint16_t)(q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q));
+}
+
 template <typename T>
 __global__ void fbm3_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint32_t salt) {
     const uint32_t n = 1u << log2n;
@@ -215,7 +221,7 @@ extern "C" int cloud_volume_create(const cloud_volume_desc *desc, void *stream, 
     clear_error();
     if (!desc || !out) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: null pointer");
     const cloud_volume_desc &d = *desc;
-    if (d.precision < CLOUD_PRECISION_FP32 || d.precision > CLOUD_PRECISION_BF16)
+    if (d.precision < CLOUD_PRECISION_FP32 || d.precision > CLOUD_PRECISION_UNORM16)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: bad precision");
     if (d.density_mode != CLOUD_DENSITY_NOISE && d.density_mode != CLOUD_DENSITY_CONSTANT)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: bad density_mode");
@@ -230,9 +236,9 @@ extern "C" int cloud_volume_create(const cloud_volume_desc *desc, void *stream, 
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: detail_n must be 0 or 2^k in [16,1024]");
         if (d.weather_n && !pow2_in(d.weather_n, 16, 4096))
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: weather_n must be 0 or 2^k in [16,4096]");
-        if (!(d.base_period_m > 0) || (d.detail_n && !(d.detail_period_m > 0)) ||
-            (d.weather_n && !(d.weather_period_m > 0)))
-            return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: periods must be > 0");
+        if (!(d.base_period_m >= 1.0) || (d.detail_n && !(d.detail_period_m >= 1.0)) ||
+            (d.weather_n && !(d.weather_period_m >= 1.0)))
+            return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: periods must be >= 1 m");
         if (!(d.coverage >= 0.0 && d.coverage < 1.0))
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_create: coverage outside [0,1)");
     } else if (!(d.constant_density >= 0.0)) {
@@ -256,7 +262,8 @@ extern "C" int cloud_volume_create(const cloud_volume_desc *desc, void *stream, 
         if (!rc) {
             if (d.precision == CLOUD_PRECISION_FP32) rc = generate<float>(v, s);
             else if (d.precision == CLOUD_PRECISION_FP16) rc = generate<__half>(v, s);
-            else rc = generate<__nv_bfloat16>(v, s);
+            else if (d.precision == CLOUD_PRECISION_BF16) rc = generate<__nv_bfloat16>(v, s);
+            else rc = generate<uint16_t>(v, s);
         }
         if (rc) {
             cudaStreamSynchronize(s);
@@ -283,7 +290,8 @@ extern "C" int cloud_volume_export(const cloud_volume *vol, float *base, float *
     switch (vol->desc.precision) {
         case CLOUD_PRECISION_FP32: return decode_all<float>(vol, base, detail, weather, s);
         case CLOUD_PRECISION_FP16: return decode_all<__half>(vol, base, detail, weather, s);
-        default: return decode_all<__nv_bfloat16>(vol, base, detail, weather, s);
+        case CLOUD_PRECISION_BF16: return decode_all<__nv_bfloat16>(vol, base, detail, weather, s);
+        default: return decode_all<uint16_t>(vol, base, detail, weather, s);
     }
 }
 

@@ -39,7 +39,9 @@ def test_motion_parity(api, oracle, w, h):
         prev, cur = I.orbit_camera(f - 1, 3), I.orbit_camera(f, 3)
         got = api.motion(vol, prm, prev, cur, w, h).cpu().numpy()
         ref = oracle.motion(desc, prm, prev, cur, w, h)
-        assert np.abs(got - ref).max() <= 1e-4
+        err = np.abs(got - ref).max()
+        print(f"motion {w}x{h} frame {f}: max abs err {err:.3e} px")
+        assert err <= 1e-4
     # a camera turned away: every point is behind the previous camera
     prev = I.camera((0.0, 0.0, 500.0), 180.0, 20.0, 60.0)
     cur = I.camera((0.0, 0.0, 500.0), 0.0, 20.0, 60.0)
@@ -72,7 +74,10 @@ def test_taa_rejects_overlap(api):
         api.taa(buf, buf, mot, out=buf)
 
 
-@pytest.mark.parametrize("fmt,tol", [("fp32", 1e-4), ("fp16", 3e-3)])
+# FP16 history: each resolve rounds to 2^-11 relative (values <= 2) and the
+# blend carries 0.9 of it forward, so the chain error is bounded by
+# 2^-11 * 2 / 0.1 ~ 1e-2 (plus the render tolerance).
+@pytest.mark.parametrize("fmt,tol", [("fp32", 1e-4), ("fp16", 1e-2)])
 def test_session_matches_oracle_chain(api, oracle, fmt, tol):
     import torch
     desc = I.volume_desc("full", seed=3)
@@ -91,5 +96,6 @@ def test_session_matches_oracle_chain(api, oracle, fmt, tol):
                 else np.zeros((h, w, 2)))
         ohist = oracle.taa(ohist, ocur, omot, blend=0.1)
         err = np.abs(host.numpy().astype(np.float64) - ohist).max()
+        print(f"session {fmt} frame {f}: max abs err {err:.3e}")
         assert err <= tol, (f, err)
     sess.close()
