@@ -59,9 +59,9 @@ constexpr float kCentre = 0.5f;
 struct cloud_volume {
     cloud_volume_desc desc;
     int log2_base, log2_detail, log2_weather;  // 0 when the tile is absent
-    void *base;      // device, base_n^3 texels of the storage precision
-    void *detail;    // device or nullptr
-    void *weather;   // device or nullptr
+    void *base;      // device, base_n^3 corner-packed records of the storage precision
+    void *detail;    // device or nullptr (detail_n^3 records)
+    void *weather;   // device or nullptr (weather_n^2 records)
     int device;
 };
 
@@ -126,11 +126,20 @@ __device__ __forceinline__ df df_rsqrt(df a) {
 __device__ __forceinline__ bool df_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ df df_max(df a, df b) { return df_gt(a, b) ? a : b; }
 __device__ __forceinline__ df df_min(df a, df b) { return df_gt(a, b) ? b : a; }
-// round(a) modulo 2^32 (fixed-point wrap); |a| < 2^62.
+// An integer-valued float modulo 2^32, from its bit pattern (integer ALU
+// only; a 64-bit float-to-integer conversion would use the slow FP64 pipe).
+__device__ __forceinline__ uint32_t int_float_mod32(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xFFu) - 150;  // v = m 2^e, m the 24-bit significand
+    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+    const uint32_t mag = e >= 0 ? (e < 32 ? m << e : 0u) : (e > -24 ? m >> -e : 0u);
+    return (b >> 31) ? 0u - mag : mag;
+}
+// round(a) modulo 2^32 (fixed-point wrap) of a double-float; |a| < 2^100.
 __device__ __forceinline__ uint32_t df_to_u32(df a) {
-    const long long h = __float2ll_rn(a.hi);
-    const float rem = (a.hi - (float)h) + a.lo;
-    return (uint32_t)h + (uint32_t)__float2int_rn(rem);
+    const float hr = rintf(a.hi);
+    const float rem = rintf((a.hi - hr) + a.lo);
+    return int_float_mod32(hr) + int_float_mod32(rem);
 }
 
 // Host: split an FP64 value into a double-float pair.
@@ -152,7 +161,61 @@ inline void split_df10(double v, float *hi, float *lo) {
     *lo = (float)(v - (double)*hi);
 }
 
-// Texel loads through the read-only path, decoded to float.
+// ---------------------------------------------------------------------------
+// Corner-packed tiles.  Record k of an N^3 tile holds the 8 texels of the
+// trilinear footprint whose lowest corner is texel k, with the periodic wrap
+// already applied (corner c = dx + 2 dy + 4 dz); record k of an N^2 tile holds
+// the 4 texels of the bilinear footprint (c = dx + 2 dy).  One lookup is then
+// one contiguous record load (16 B for 16-bit texels, 32 B for FP32) instead
+// of 8 (or 4) scattered texel loads.  Corner 0 of record k is texel k.
+//
+// The loaders return the corners in an affine "raw" form r = texel + bias so
+// that a 16-bit fixed-point texel decodes with bit operations only; the
+// interpolated raw value minus `raw_bias<T>()` is the centred texel value.
+template <typename T>
+__host__ __device__ constexpr float raw_bias() { return 0.0f; }
+template <>
+__host__ __device__ constexpr float raw_bias<uint16_t>() { return 1.5f; }  // 1 + q 2^-16 = v + 1/2 + 1
+
+__device__ __forceinline__ void load_rec8(const float *tile, uint32_t rec, float c[8]) {
+    const float4 *p = reinterpret_cast<const float4 *>(tile) + 2 * (size_t)rec;
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+__device__ __forceinline__ void unpack16(uint32_t w, const __half *, float &lo, float &hi) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    lo = f.x;
+    hi = f.y;
+}
+__device__ __forceinline__ void unpack16(uint32_t w, const __nv_bfloat16 *, float &lo, float &hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xFFFF0000u);
+}
+__device__ __forceinline__ void unpack16(uint32_t w, const uint16_t *, float &lo, float &hi) {
+    lo = __uint_as_float(0x3F800000u | ((w << 7) & 0x007FFF80u));  // 1 + q_lo 2^-16
+    hi = __uint_as_float(0x3F800000u | ((w >> 9) & 0x007FFF80u));  // 1 + q_hi 2^-16
+}
+template <typename T>
+__device__ __forceinline__ void load_rec8(const T *tile, uint32_t rec, float c[8]) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(tile) + rec);
+    unpack16(r.x, tile, c[0], c[1]);
+    unpack16(r.y, tile, c[2], c[3]);
+    unpack16(r.z, tile, c[4], c[5]);
+    unpack16(r.w, tile, c[6], c[7]);
+}
+__device__ __forceinline__ void load_rec4(const float *tile, uint32_t rec, float c[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(tile) + rec);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+}
+template <typename T>
+__device__ __forceinline__ void load_rec4(const T *tile, uint32_t rec, float c[4]) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2 *>(tile) + rec);
+    unpack16(r.x, tile, c[0], c[1]);
+    unpack16(r.y, tile, c[2], c[3]);
+}
+
+// Plain (unpacked) texel loads, decoded to the centred value.
 __device__ __forceinline__ float load_texel(const float *p, uint32_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_texel(const __half *p, uint32_t i) {
     return __half2float(__ldg(p + i));

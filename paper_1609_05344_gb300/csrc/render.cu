@@ -54,38 +54,32 @@ __device__ __forceinline__ float frac23(uint32_t f) {
     return __uint_as_float((f >> 9) | 0x3F800000u) - 1.0f;
 }
 
-// Trilinear sample of a 2^L cube at fixed-point coordinates (wrap by masking).
+// Trilinear sample of a corner-packed 2^L cube at fixed-point coordinates:
+// the record index is the top L bits of each coordinate, the weights the next
+// 23 bits.  Returns the centred texel value (fBm - 1/2).
 template <typename T>
-__device__ __forceinline__ float sample3(const T *__restrict__ tex, int L, uint32_t cx, uint32_t cy,
+__device__ __forceinline__ float sample3(const T *__restrict__ tile, int L, uint32_t cx, uint32_t cy,
                                          uint32_t cz) {
     const int sh = 32 - L;
-    const uint32_t mask = (1u << L) - 1u;
-    const uint32_t x0 = cx >> sh, y0 = cy >> sh, z0 = cz >> sh;
-    const uint32_t x1 = (x0 + 1u) & mask, y1 = (y0 + 1u) & mask, z1 = (z0 + 1u) & mask;
+    const uint32_t rec = ((cz >> sh) << (2 * L)) | ((cy >> sh) << L) | (cx >> sh);
     const float fx = frac23(cx << L), fy = frac23(cy << L), fz = frac23(cz << L);
-    const uint32_t r00 = (z0 << (2 * L)) | (y0 << L), r01 = (z0 << (2 * L)) | (y1 << L);
-    const uint32_t r10 = (z1 << (2 * L)) | (y0 << L), r11 = (z1 << (2 * L)) | (y1 << L);
-    const float a00 = load_texel(tex, r00 | x0), b00 = load_texel(tex, r00 | x1);
-    const float a01 = load_texel(tex, r01 | x0), b01 = load_texel(tex, r01 | x1);
-    const float a10 = load_texel(tex, r10 | x0), b10 = load_texel(tex, r10 | x1);
-    const float a11 = load_texel(tex, r11 | x0), b11 = load_texel(tex, r11 | x1);
-    const float c00 = fmaf(fx, b00 - a00, a00), c01 = fmaf(fx, b01 - a01, a01);
-    const float c10 = fmaf(fx, b10 - a10, a10), c11 = fmaf(fx, b11 - a11, a11);
-    const float c0 = fmaf(fy, c01 - c00, c00), c1 = fmaf(fy, c11 - c10, c10);
-    return fmaf(fz, c1 - c0, c0);
+    float c[8];
+    load_rec8(tile, rec, c);
+    const float c00 = fmaf(fx, c[1] - c[0], c[0]), c10 = fmaf(fx, c[3] - c[2], c[2]);
+    const float c01 = fmaf(fx, c[5] - c[4], c[4]), c11 = fmaf(fx, c[7] - c[6], c[6]);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    return fmaf(fz, c1 - c0, c0) - raw_bias<T>();
 }
 
 template <typename T>
-__device__ __forceinline__ float sample2(const T *__restrict__ tex, int L, uint32_t cx, uint32_t cy) {
+__device__ __forceinline__ float sample2(const T *__restrict__ tile, int L, uint32_t cx, uint32_t cy) {
     const int sh = 32 - L;
-    const uint32_t mask = (1u << L) - 1u;
-    const uint32_t x0 = cx >> sh, y0 = cy >> sh;
-    const uint32_t x1 = (x0 + 1u) & mask, y1 = (y0 + 1u) & mask;
+    const uint32_t rec = ((cy >> sh) << L) | (cx >> sh);
     const float fx = frac23(cx << L), fy = frac23(cy << L);
-    const float a0 = load_texel(tex, (y0 << L) | x0), b0 = load_texel(tex, (y0 << L) | x1);
-    const float a1 = load_texel(tex, (y1 << L) | x0), b1 = load_texel(tex, (y1 << L) | x1);
-    const float c0 = fmaf(fx, b0 - a0, a0), c1 = fmaf(fx, b1 - a1, a1);
-    return fmaf(fy, c1 - c0, c0);
+    float c[4];
+    load_rec4(tile, rec, c);
+    const float c0 = fmaf(fx, c[1] - c[0], c[0]), c1 = fmaf(fx, c[3] - c[2], c[2]);
+    return fmaf(fy, c1 - c0, c0) - raw_bias<T>();
 }
 
 // Density at a sample (Sec. 1 "the density is sampled"):
@@ -126,7 +120,7 @@ __device__ __forceinline__ df df_addf(df a, float b) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p,
+__global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ MarchParams p,
                                                     const T *__restrict__ base,
                                                     const T *__restrict__ detail,
                                                     const T *__restrict__ weather,

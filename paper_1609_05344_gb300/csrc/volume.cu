@@ -127,11 +127,46 @@ __global__ void fbm2_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint3
     }
 }
 
+// Corner-packing of a generated tile (see common.cuh).
 template <typename T>
-__global__ void decode_kernel(const T *__restrict__ in, float *__restrict__ out, uint64_t n) {
+__global__ void pack3_kernel(const T *__restrict__ plain, T *__restrict__ packed, int log2n) {
+    const uint32_t mask = (1u << log2n) - 1u;
+    const uint64_t total = 1ull << (3 * log2n);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n) & mask,
+                       z = (uint32_t)(i >> (2 * log2n));
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t xx = (x + (c & 1)) & mask, yy = (y + ((c >> 1) & 1)) & mask,
+                           zz = (z + (c >> 2)) & mask;
+            packed[8 * i + c] = plain[((uint64_t)zz << (2 * log2n)) | (yy << log2n) | xx];
+        }
+    }
+}
+
+template <typename T>
+__global__ void pack2_kernel(const T *__restrict__ plain, T *__restrict__ packed, int log2n) {
+    const uint32_t mask = (1u << log2n) - 1u;
+    const uint64_t total = 1ull << (2 * log2n);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t xx = (x + (c & 1)) & mask, yy = (y + (c >> 1)) & mask;
+            packed[4 * i + c] = plain[(yy << log2n) | xx];
+        }
+    }
+}
+
+// Texel k of a packed tile is corner 0 of record k.
+template <typename T>
+__global__ void decode_kernel(const T *__restrict__ packed, int stride, float *__restrict__ out,
+                              uint64_t n) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = load_texel(in, (uint32_t)i) + kCentre;
+        out[i] = load_texel(packed, (uint32_t)(stride * i)) + kCentre;
 }
 
 __global__ void hash4_kernel(const uint4 *__restrict__ keys, uint32_t *__restrict__ out, int64_t n) {
@@ -148,42 +183,50 @@ unsigned grid_for(uint64_t n, unsigned block) {
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+// Generates each tile into a plain scratch array, then corner-packs it.
 template <typename T>
 int generate(cloud_volume *v, cudaStream_t s) {
     const cloud_volume_desc &d = v->desc;
     const uint64_t nb = 1ull << (3 * v->log2_base);
-    fbm3_kernel<T><<<grid_for(nb, 256), 256, 0, s>>>((T *)v->base, v->log2_base, d.seed, kSaltBase);
-    if (int rc = check_launch("fbm3 base")) return rc;
-    if (v->detail) {
-        const uint64_t nd = 1ull << (3 * v->log2_detail);
-        fbm3_kernel<T><<<grid_for(nd, 256), 256, 0, s>>>((T *)v->detail, v->log2_detail, d.seed,
-                                                        kSaltDetail);
-        if (int rc = check_launch("fbm3 detail")) return rc;
+    const uint64_t nd = v->detail ? 1ull << (3 * v->log2_detail) : 0;
+    const uint64_t nw = v->weather ? 1ull << (2 * v->log2_weather) : 0;
+    const uint64_t most = nb > nd ? (nb > nw ? nb : nw) : (nd > nw ? nd : nw);
+    T *tmp = nullptr;
+    int rc = check_cuda(cudaMalloc(&tmp, most * sizeof(T)), "cudaMalloc generation scratch");
+    if (rc) return rc;
+    fbm3_kernel<T><<<grid_for(nb, 256), 256, 0, s>>>(tmp, v->log2_base, d.seed, kSaltBase);
+    pack3_kernel<T><<<grid_for(nb, 256), 256, 0, s>>>(tmp, (T *)v->base, v->log2_base);
+    rc = check_launch("generate base");
+    if (!rc && v->detail) {
+        fbm3_kernel<T><<<grid_for(nd, 256), 256, 0, s>>>(tmp, v->log2_detail, d.seed, kSaltDetail);
+        pack3_kernel<T><<<grid_for(nd, 256), 256, 0, s>>>(tmp, (T *)v->detail, v->log2_detail);
+        rc = check_launch("generate detail");
     }
-    if (v->weather) {
-        const uint64_t nw = 1ull << (2 * v->log2_weather);
-        fbm2_kernel<T><<<grid_for(nw, 256), 256, 0, s>>>((T *)v->weather, v->log2_weather, d.seed,
-                                                        kSaltWeather);
-        if (int rc = check_launch("fbm2 weather")) return rc;
+    if (!rc && v->weather) {
+        fbm2_kernel<T><<<grid_for(nw, 256), 256, 0, s>>>(tmp, v->log2_weather, d.seed, kSaltWeather);
+        pack2_kernel<T><<<grid_for(nw, 256), 256, 0, s>>>(tmp, (T *)v->weather, v->log2_weather);
+        rc = check_launch("generate weather");
     }
-    return CLOUD_OK;
+    const int rs = check_cuda(cudaStreamSynchronize(s), "generation");
+    cudaFree(tmp);
+    return rc ? rc : rs;
 }
 
 template <typename T>
 int decode_all(const cloud_volume *v, float *base, float *detail, float *weather, cudaStream_t s) {
     if (base && v->base) {
         const uint64_t n = 1ull << (3 * v->log2_base);
-        decode_kernel<T><<<grid_for(n, 256), 256, 0, s>>>((const T *)v->base, base, n);
+        decode_kernel<T><<<grid_for(n, 256), 256, 0, s>>>((const T *)v->base, 8, base, n);
         if (int rc = check_launch("decode base")) return rc;
     }
     if (detail && v->detail) {
         const uint64_t n = 1ull << (3 * v->log2_detail);
-        decode_kernel<T><<<grid_for(n, 256), 256, 0, s>>>((const T *)v->detail, detail, n);
+        decode_kernel<T><<<grid_for(n, 256), 256, 0, s>>>((const T *)v->detail, 8, detail, n);
         if (int rc = check_launch("decode detail")) return rc;
     }
     if (weather && v->weather) {
         const uint64_t n = 1ull << (2 * v->log2_weather);
-        decode_kernel<T><<<grid_for(n, 256), 256, 0, s>>>((const T *)v->weather, weather, n);
+        decode_kernel<T><<<grid_for(n, 256), 256, 0, s>>>((const T *)v->weather, 4, weather, n);
         if (int rc = check_launch("decode weather")) return rc;
     }
     return CLOUD_OK;
@@ -254,11 +297,12 @@ extern "C" int cloud_volume_create(const cloud_volume_desc *desc, void *stream, 
         v->log2_base = ilog2(d.base_n);
         v->log2_detail = d.detail_n ? ilog2(d.detail_n) : 0;
         v->log2_weather = d.weather_n ? ilog2(d.weather_n) : 0;
-        int rc = check_cuda(cudaMalloc(&v->base, eb << (3 * v->log2_base)), "cudaMalloc base");
+        // corner-packed records: 8 texels per 3-D record, 4 per 2-D record
+        int rc = check_cuda(cudaMalloc(&v->base, (8 * eb) << (3 * v->log2_base)), "cudaMalloc base");
         if (!rc && d.detail_n)
-            rc = check_cuda(cudaMalloc(&v->detail, eb << (3 * v->log2_detail)), "cudaMalloc detail");
+            rc = check_cuda(cudaMalloc(&v->detail, (8 * eb) << (3 * v->log2_detail)), "cudaMalloc detail");
         if (!rc && d.weather_n)
-            rc = check_cuda(cudaMalloc(&v->weather, eb << (2 * v->log2_weather)), "cudaMalloc weather");
+            rc = check_cuda(cudaMalloc(&v->weather, (4 * eb) << (2 * v->log2_weather)), "cudaMalloc weather");
         if (!rc) {
             if (d.precision == CLOUD_PRECISION_FP32) rc = generate<float>(v, s);
             else if (d.precision == CLOUD_PRECISION_FP16) rc = generate<__half>(v, s);
