@@ -119,18 +119,55 @@ __device__ __forceinline__ df df_addf(df a, float b) {
     return fast_two_sum(s.hi, s.lo + a.lo);
 }
 
-template <typename T>
+constexpr int kAxes = kLatticeAxes + 1;  // lattice axes + height above the layer bottom
+constexpr int kChunk = 8;                // view steps per warp-cooperative chunk
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Per-warp shared scratch of the march: each lane's start coordinates and
+// per-step increments, the chunk's view densities, light-march sums and the
+// list of (step, lane) pairs that need a light march.
+struct WarpScratch {
+    uint32_t c0[kAxes][32];
+    uint32_t e[kAxes][32];
+    float rho[kChunk][32];
+    float lsum[kChunk][32];
+    uint16_t pairs[kChunk * 32];
+};
+
+// sigma D of one step, rounded the same way wherever it is recomputed
+__device__ __forceinline__ float step_depth(float absorption, float rho, float D) {
+    return __fmul_rn(__fmul_rn(absorption, rho), D);
+}
+
+// The march of one 16x8 tile (4 warps, one pixel per lane).  View steps are
+// processed in chunks of kChunk:
+//   A  each lane evaluates its view densities and its early out (the optical
+//      depth does not depend on the lighting);
+//   B  the warp shares out every (step, lane) light march with density > 0
+//      over all 32 lanes, so lanes whose own rays are empty, finished or
+//      outside the layer do useful work;
+//   C  each lane integrates its steps in order with the light sums from B.
+// The arithmetic of every sample is the same as a per-lane march.
+template <typename T, int LS>
 __global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ MarchParams p,
-                                                    const T *__restrict__ base,
-                                                    const T *__restrict__ detail,
-                                                    const T *__restrict__ weather,
-                                                    float4 *__restrict__ out,
-                                                    unsigned long long *__restrict__ counter) {
+                                                       const T *__restrict__ base,
+                                                       const T *__restrict__ detail,
+                                                       const T *__restrict__ weather,
+                                                       float4 *__restrict__ out,
+                                                       unsigned long long *__restrict__ counter) {
+    __shared__ WarpScratch scratch[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpScratch &ws = scratch[warp];
     const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside = x < p.width && y < p.height;
+    const int nlight = LS >= 0 ? LS : p.light_steps;
     unsigned long long n_look = 0;
-    if (x < p.width && y < p.height) {
+    uint32_t c[kLatticeAxes] = {}, e[kLatticeAxes] = {};
+    int32_t hq = 0, eh = 0;
+    float Df = 0.0f, phase = 0.0f;
+    bool alive = false;
+    if (inside) {
         // --- a1: pixel ray and layer clip (double-float) ---------------------
         // p(lambda) = o + lambda v with v unnormalised; t = lambda |v|.
         const float xf = (float)x, yf = (float)y;
@@ -145,18 +182,16 @@ __global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ M
         const df rn = df_rsqrt(n2);  // 1 / |v|
         const df lam_max = df_mul({p.tmax_h, p.tmax_l}, rn);
         df lam0 = {0.0f, 0.0f}, lam1 = lam_max;
-        bool hit;
         if (fabsf(v[2].hi) * rn.hi < 1e-8f) {
-            hit = p.cam_in_layer != 0;
+            alive = p.cam_in_layer != 0;
         } else {
             const df inv = df_recip(v[2]);
             const df ll = df_mul({p.zlo_h, p.zlo_l}, inv), lh = df_mul({p.zhi_h, p.zhi_l}, inv);
             lam0 = df_max(df_min(ll, lh), lam0);
             lam1 = df_min(df_max(ll, lh), lam_max);
-            hit = df_gt(lam1, lam0);
+            alive = df_gt(lam1, lam0);
         }
-        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (hit) {
+        if (alive) {
             // --- a2: jittered start offset (Sec. 3.2) ---------------------------
             const df D = df_mul(df_add(lam1, df_neg(lam0)), {p.invn_h, p.invn_l});
             float u = 0.5f;
@@ -170,7 +205,6 @@ __global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ M
                 pos[k] = df_add({p.oh[k], p.ol[k]}, df_mul(lam_s, v[k]));
                 dpos[k] = df_mul(D, v[k]);
             }
-            uint32_t c[kLatticeAxes], e[kLatticeAxes];
 #pragma unroll
             for (int a = 0; a < kLatticeAxes; ++a) {
                 const int comp = a < 6 ? a % 3 : a - 6;
@@ -180,64 +214,114 @@ __global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ M
             }
             // height above the layer bottom: (o_z - slab_lo) + lambda v_z, in 2^-16 m
             const df hrel = df_add(df_mul(lam_s, v[2]), df_neg({p.zlo_h, p.zlo_l}));
-            int32_t hq = (int32_t)df_to_u32({hrel.hi * 65536.0f, hrel.lo * 65536.0f});
-            const int32_t eh = (int32_t)df_to_u32({dpos[2].hi * 65536.0f, dpos[2].lo * 65536.0f});
+            hq = (int32_t)df_to_u32({hrel.hi * 65536.0f, hrel.lo * 65536.0f});
+            eh = (int32_t)df_to_u32({dpos[2].hi * 65536.0f, dpos[2].lo * 65536.0f});
             const float vlen = n2.hi * rn.hi;
-            const float Df = D.hi * vlen;
-            // --- a5: phase, hoisted per ray ------------------------------------
+            Df = D.hi * vlen;
+            // --- a5: phase function, hoisted per ray ----------------------------
             const float mu = (v[0].hi * p.sun[0] + v[1].hi * p.sun[1] + v[2].hi * p.sun[2]) * rn.hi;
             const float g = p.hg_g;
             const float den = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
-            const float phase = (1.0f - g * g) / (4.0f * 3.14159265358979f * den * sqrtf(den));
-            float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-            for (int i = 0; i < p.steps; ++i) {
+            phase = (1.0f - g * g) / (4.0f * 3.14159265358979f * den * sqrtf(den));
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < kLatticeAxes; ++a) {
+        ws.c0[a][lane] = c[a];
+        ws.e[a][lane] = e[a];
+    }
+    ws.c0[kLatticeAxes][lane] = (uint32_t)hq;
+    ws.e[kLatticeAxes][lane] = (uint32_t)eh;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    for (int i0 = 0; i0 < p.steps && __any_sync(kFull, alive); i0 += kChunk) {
+        // --- A: view densities and early out --------------------------------
+        uint32_t act = 0;
+        int nA = 0;
+        if (alive) {
+            float tau_a = tau;
+#pragma unroll
+            for (int k = 0; k < kChunk; ++k) {
+                if (i0 + k >= p.steps) break;
                 // --- a3: density lookup ---------------------------------------
                 const float rho = density(p, base, detail, weather, c, hq);
-                ++n_look;
+                ws.rho[k][lane] = rho;
+                nA = k + 1;
                 if (rho > 0.0f) {
-                    // --- a4: light march towards the sun (Sec. 1) ----------------
-                    float rho_sum = 0.0f;
-                    for (int j = 0; j < p.light_steps; ++j) {
-                        uint32_t cj[kLatticeAxes];
-#pragma unroll
-                        for (int a = 0; a < kLatticeAxes; ++a) cj[a] = c[a] + p.loff[j][a];
-                        rho_sum += density(p, base, detail, weather, cj, hq + p.lh[j]);
-                    }
-                    n_look += p.light_steps;
-                    // --- a5: in-scattered light ---------------------------------
-                    const float sun_t = expf(-p.absorption * p.light_step * rho_sum) * phase;
-                    const float lr = fmaf(p.sun_rad[0], sun_t, p.ambient[0]);
-                    const float lg = fmaf(p.sun_rad[1], sun_t, p.ambient[1]);
-                    const float lb = fmaf(p.sun_rad[2], sun_t, p.ambient[2]);
-                    // --- a6: per-step integral (Sec. 3.1) ----------------------
-                    const float sd = p.absorption * rho * Df;
-                    float wgt;
-                    if (p.integration == CLOUD_INTEGRATE_ANALYTIC) {
-                        wgt = expf(-tau) * -expm1f(-sd);
-                        tau += sd;
-                    } else {
-                        tau += sd;
-                        wgt = expf(-tau) * sd;
-                    }
-                    cr = fmaf(wgt, lr, cr);
-                    cg = fmaf(wgt, lg, cg);
-                    cb = fmaf(wgt, lb, cb);
+                    act |= 1u << k;
+                    tau_a = __fadd_rn(tau_a, step_depth(p.absorption, rho, Df));
                 }
-                // --- a7: early out once alpha is ~1 (Sec. 1) --------------------
-                if (tau >= p.tau_max) break;
 #pragma unroll
                 for (int a = 0; a < kLatticeAxes; ++a) c[a] += e[a];
                 hq += eh;
+                // --- a7: early out once alpha is ~1 (Sec. 1) --------------------
+                if (tau_a >= p.tau_max) {
+                    alive = false;
+                    break;
+                }
             }
-            res = make_float4(cr, cg, cb, -expm1f(-tau));
+            n_look += nA + nlight * __popc(act);
         }
-        // --- a8: premultiplied RGBA, one 16-byte store -------------------------
-        out[(size_t)y * p.width + x] = res;
+        // --- B: light marches shared out over the warp (a4, Sec. 1) ----------
+        unsigned offs[kChunk + 1];
+        offs[0] = 0;
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+            const unsigned m = __ballot_sync(kFull, (act >> k) & 1u);
+            if ((act >> k) & 1u) ws.pairs[offs[k] + __popc(m & lt_mask)] = (uint16_t)((k << 5) | lane);
+            offs[k + 1] = offs[k] + __popc(m);
+        }
+        __syncwarp();
+        for (unsigned q = lane; q < offs[kChunk]; q += 32) {
+            const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
+            const uint32_t i = (uint32_t)(i0 + (int)k);
+            uint32_t cs[kLatticeAxes];
+#pragma unroll
+            for (int a = 0; a < kLatticeAxes; ++a) cs[a] = ws.c0[a][ow] + i * ws.e[a][ow];
+            const int32_t hs = (int32_t)(ws.c0[kLatticeAxes][ow] + i * ws.e[kLatticeAxes][ow]);
+            float rho_sum = 0.0f;
+#pragma unroll
+            for (int j = 0; j < (LS >= 0 ? LS : CLOUD_MAX_LIGHT_STEPS); ++j) {
+                if (LS < 0 && j >= nlight) break;
+                uint32_t cj[kLatticeAxes];
+#pragma unroll
+                for (int a = 0; a < kLatticeAxes; ++a) cj[a] = cs[a] + p.loff[j][a];
+                rho_sum += density(p, base, detail, weather, cj, hs + p.lh[j]);
+            }
+            ws.lsum[k][ow] = rho_sum;
+        }
+        __syncwarp();
+        // --- C: in-scattered light and the per-step integral, in step order ---
+        for (int k = 0; k < nA; ++k) {
+            if (!((act >> k) & 1u)) continue;
+            const float rho = ws.rho[k][lane];
+            // --- a5: in-scattered light ---------------------------------------
+            const float sun_t = expf(-p.absorption * p.light_step * ws.lsum[k][lane]) * phase;
+            const float lr = fmaf(p.sun_rad[0], sun_t, p.ambient[0]);
+            const float lg = fmaf(p.sun_rad[1], sun_t, p.ambient[1]);
+            const float lb = fmaf(p.sun_rad[2], sun_t, p.ambient[2]);
+            // --- a6: per-step integral (Sec. 3.1) ------------------------------
+            const float sd = step_depth(p.absorption, rho, Df);
+            float wgt;
+            if (p.integration == CLOUD_INTEGRATE_ANALYTIC) {
+                wgt = expf(-tau) * -expm1f(-sd);
+                tau = __fadd_rn(tau, sd);
+            } else {
+                tau = __fadd_rn(tau, sd);
+                wgt = expf(-tau) * sd;
+            }
+            cr = fmaf(wgt, lr, cr);
+            cg = fmaf(wgt, lg, cg);
+            cb = fmaf(wgt, lb, cb);
+        }
+        __syncwarp();
     }
+    // --- a8: premultiplied RGBA, one 16-byte store ------------------------------
+    if (inside) out[(size_t)y * p.width + x] = make_float4(cr, cg, cb, -expm1f(-tau));
     if (counter) {
         unsigned long long v = n_look;
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, s);
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(kFull, v, s);
         if (lane == 0 && v) atomicAdd(counter, v);
     }
 }
@@ -335,6 +419,19 @@ int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
     return CLOUD_OK;
 }
 
+// The common light-march length (6, Sec. 1) is compiled with its offsets as
+// constants; any other length uses the generic loop.
+template <typename T>
+int launch_typed(const MarchParams &p, const cloud_volume *vol, float *out,
+                 unsigned long long *counter, dim3 grid, cudaStream_t s) {
+    const T *b = (const T *)vol->base, *d = (const T *)vol->detail, *w = (const T *)vol->weather;
+    if (p.light_steps == 6)
+        march_kernel<T, 6><<<grid, 128, 0, s>>>(p, b, d, w, (float4 *)out, counter);
+    else
+        march_kernel<T, -1><<<grid, 128, 0, s>>>(p, b, d, w, (float4 *)out, counter);
+    return check_launch("march_kernel");
+}
+
 int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
                   int width, int height, int steps, int light_steps, int jitter_frame,
                   int integration, float *out, unsigned long long *counter, cudaStream_t s) {
@@ -350,28 +447,14 @@ int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_
     const dim3 grid((width + 15) / 16, (height + 7) / 8);
     switch (vol->desc.precision) {
         case CLOUD_PRECISION_FP32:
-            march_kernel<float><<<grid, 128, 0, s>>>(p, (const float *)vol->base,
-                                                     (const float *)vol->detail,
-                                                     (const float *)vol->weather, (float4 *)out,
-                                                     counter);
-            break;
+            return launch_typed<float>(p, vol, out, counter, grid, s);
         case CLOUD_PRECISION_FP16:
-            march_kernel<__half><<<grid, 128, 0, s>>>(p, (const __half *)vol->base,
-                                                      (const __half *)vol->detail,
-                                                      (const __half *)vol->weather, (float4 *)out,
-                                                      counter);
-            break;
+            return launch_typed<__half>(p, vol, out, counter, grid, s);
         case CLOUD_PRECISION_BF16:
-            march_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(
-                p, (const __nv_bfloat16 *)vol->base, (const __nv_bfloat16 *)vol->detail,
-                (const __nv_bfloat16 *)vol->weather, (float4 *)out, counter);
-            break;
+            return launch_typed<__nv_bfloat16>(p, vol, out, counter, grid, s);
         default:
-            march_kernel<uint16_t><<<grid, 128, 0, s>>>(
-                p, (const uint16_t *)vol->base, (const uint16_t *)vol->detail,
-                (const uint16_t *)vol->weather, (float4 *)out, counter);
+            return launch_typed<uint16_t>(p, vol, out, counter, grid, s);
     }
-    return check_launch("march_kernel");
 }
 
 }  // namespace cloudvol
