@@ -54,38 +54,36 @@ __device__ __forceinline__ float frac23(uint32_t f) {
     return __uint_as_float((f >> 9) | 0x3F800000u) - 1.0f;
 }
 
-// Trilinear sample of a corner-packed 2^L cube at fixed-point coordinates:
-// the record index is the top L bits of each coordinate, the weights the next
-// 23 bits.  Returns the centred texel value (fBm - 1/2).
-template <typename T>
-__device__ __forceinline__ float sample3(const T *__restrict__ tile, int L, uint32_t cx, uint32_t cy,
-                                         uint32_t cz) {
+// Corner-packed sampling at fixed-point coordinates: the record index is the
+// top L bits of each coordinate, the interpolation weights the next 23 bits.
+__device__ __forceinline__ uint32_t rec3(int L, uint32_t cx, uint32_t cy, uint32_t cz) {
     const int sh = 32 - L;
-    const uint32_t rec = ((cz >> sh) << (2 * L)) | ((cy >> sh) << L) | (cx >> sh);
+    return ((cz >> sh) << (2 * L)) | ((cy >> sh) << L) | (cx >> sh);
+}
+__device__ __forceinline__ uint32_t rec2(int L, uint32_t cx, uint32_t cy) {
+    const int sh = 32 - L;
+    return ((cy >> sh) << L) | (cx >> sh);
+}
+__device__ __forceinline__ float trilerp(const float c[8], int L, uint32_t cx, uint32_t cy,
+                                         uint32_t cz) {
     const float fx = frac23(cx << L), fy = frac23(cy << L), fz = frac23(cz << L);
-    float c[8];
-    load_rec8(tile, rec, c);
     const float c00 = fmaf(fx, c[1] - c[0], c[0]), c10 = fmaf(fx, c[3] - c[2], c[2]);
     const float c01 = fmaf(fx, c[5] - c[4], c[4]), c11 = fmaf(fx, c[7] - c[6], c[6]);
     const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return fmaf(fz, c1 - c0, c0) - raw_bias<T>();
+    return fmaf(fz, c1 - c0, c0);
 }
-
-template <typename T>
-__device__ __forceinline__ float sample2(const T *__restrict__ tile, int L, uint32_t cx, uint32_t cy) {
-    const int sh = 32 - L;
-    const uint32_t rec = ((cy >> sh) << L) | (cx >> sh);
+__device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, uint32_t cy) {
     const float fx = frac23(cx << L), fy = frac23(cy << L);
-    float c[4];
-    load_rec4(tile, rec, c);
     const float c0 = fmaf(fx, c[1] - c[0], c[0]), c1 = fmaf(fx, c[3] - c[2], c[2]);
-    return fmaf(fy, c1 - c0, c0) - raw_bias<T>();
+    return fmaf(fy, c1 - c0, c0);
 }
 
 // Density at a sample (Sec. 1 "the density is sampled"):
 //   rho = g(h) W max(0, (B - w_d Dt - c)/(1 - c)),
 // tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0.
-// Terms that cannot change a zero result are skipped (g = 0, W = 0, B <= c).
+// Samples outside the layer (g = 0) return without touching memory; otherwise
+// the three record loads are issued together so that one memory round trip
+// serves the lookup.
 template <typename T>
 __device__ __forceinline__ float density(const MarchParams &p, const T *__restrict__ base,
                                          const T *__restrict__ detail,
@@ -96,21 +94,18 @@ __device__ __forceinline__ float density(const MarchParams &p, const T *__restri
     const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
     const float g = ga * gb;
     if (g <= 0.0f) return 0.0f;
-    float w = 1.0f;
-    if (weather) {
-        w = sample2(weather, p.log2_weather, c[kWX], c[kWY]) + kCentre;
-        if (w <= 0.0f) return 0.0f;
-    }
-    const float b = sample3(base, p.log2_base, c[kBX], c[kBY], c[kBZ]);
-    float r;
+    float cb[8], cd[8], cw[4];
+    load_rec8(base, rec3(p.log2_base, c[kBX], c[kBY], c[kBZ]), cb);
+    if (detail) load_rec8(detail, rec3(p.log2_detail, c[kDX], c[kDY], c[kDZ]), cd);
+    if (weather) load_rec4(weather, rec2(p.log2_weather, c[kWX], c[kWY]), cw);
+    const float b = trilerp(cb, p.log2_base, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
+    float r = b + p.k0;
     if (detail) {
-        if (b + p.b_cut <= 0.0f) return 0.0f;  // B <= c: detail cannot raise it
-        const float dt = sample3(detail, p.log2_detail, c[kDX], c[kDY], c[kDZ]);
-        r = fmaf(-p.detail_w, dt, b + p.k0);
-    } else {
-        r = b + p.k0;
+        const float dt = trilerp(cd, p.log2_detail, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();
+        r = fmaf(-p.detail_w, dt, r);
     }
     r = fmaxf(r * p.inv_1mc, 0.0f);
+    const float w = weather ? bilerp(cw, p.log2_weather, c[kWX], c[kWY]) - raw_bias<T>() + kCentre : 1.0f;
     return g * w * r;
 }
 
@@ -118,6 +113,11 @@ __device__ __forceinline__ df df_addf(df a, float b) {
     const df s = two_sum(a.hi, b);
     return fast_two_sum(s.hi, s.lo + a.lo);
 }
+
+// CTAs per SM the march is compiled for (register budget 65536 / (128 x this)).
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS
+#define CLOUDVOL_MARCH_MIN_BLOCKS 6
+#endif
 
 constexpr int kAxes = kLatticeAxes + 1;  // lattice axes + height above the layer bottom
 constexpr int kChunk = 8;                // view steps per warp-cooperative chunk
@@ -149,7 +149,7 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 //   C  each lane integrates its steps in order with the light sums from B.
 // The arithmetic of every sample is the same as a per-lane march.
 template <typename T, int LS>
-__global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ MarchParams p,
+__global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS) march_kernel(const __grid_constant__ MarchParams p,
                                                        const T *__restrict__ base,
                                                        const T *__restrict__ detail,
                                                        const T *__restrict__ weather,
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(128, 8) march_kernel(const __grid_constant__ M
         int nA = 0;
         if (alive) {
             float tau_a = tau;
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < kChunk; ++k) {
                 if (i0 + k >= p.steps) break;
                 // --- a3: density lookup ---------------------------------------
