@@ -47,6 +47,12 @@ struct MarchParams {
     int log2_base, log2_detail, log2_weather;
     int width, height, steps, light_steps, jitter_frame, integration, constant_mode;
     int cam_in_layer;
+    // rays with d_z below miss_below (camera under the layer) or above
+    // miss_above (camera over it) cannot reach the layer within t_max
+    float miss_below, miss_above;
+    // detail coordinates = (base + half_base) << detail_shift - half_detail when
+    // the base tile period is 2^detail_shift detail periods (-1: convert separately)
+    int detail_shift;
     uint32_t jitter_key;
 };
 
@@ -160,17 +166,27 @@ __global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS) march_kernel(c
     WarpScratch &ws = scratch[warp];
     const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside = x < p.width && y < p.height;
+    const bool in_image = x < p.width && y < p.height;
+    bool inside = in_image;
     const int nlight = LS >= 0 ? LS : p.light_steps;
     unsigned long long n_look = 0;
     uint32_t c[kLatticeAxes] = {}, e[kLatticeAxes] = {};
     int32_t hq = 0, eh = 0;
     float Df = 0.0f, phase = 0.0f;
     bool alive = false;
+    const float xf = (float)x, yf = (float)y;
+    if (inside) {
+        // quick FP32 test for rays that cannot reach the layer (a 1e-4 margin
+        // keeps every undecided ray on the exact path below)
+        const float qx = fmaf(yf, p.vyh[0], fmaf(xf, p.vxh[0], p.v00h[0]));
+        const float qy = fmaf(yf, p.vyh[1], fmaf(xf, p.vxh[1], p.v00h[1]));
+        const float qz = fmaf(yf, p.vyh[2], fmaf(xf, p.vxh[2], p.v00h[2]));
+        const float dz = qz * rsqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+        if (dz < p.miss_below || dz > p.miss_above) inside = false;
+    }
     if (inside) {
         // --- a1: pixel ray and layer clip (double-float) ---------------------
         // p(lambda) = o + lambda v with v unnormalised; t = lambda |v|.
-        const float xf = (float)x, yf = (float)y;
         df v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -208,6 +224,13 @@ __global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS) march_kernel(c
 #pragma unroll
             for (int a = 0; a < kLatticeAxes; ++a) {
                 const int comp = a < 6 ? a % 3 : a - 6;
+                if (a >= kDX && a <= kDZ && p.detail_shift >= 0) {
+                    // same origin, period 2^-shift of the base tile: exact shift
+                    const int b = a - kDX;
+                    c[a] = ((c[b] + p.half_unit[b]) << p.detail_shift) - p.half_unit[a];
+                    e[a] = e[b] << p.detail_shift;
+                    continue;
+                }
                 const df k = {p.kfix_h[a], p.kfix_l[a]};
                 c[a] = df_to_u32(df_mul(pos[comp], k)) - p.half_unit[a];
                 e[a] = df_to_u32(df_mul(dpos[comp], k));
@@ -317,7 +340,7 @@ __global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS) march_kernel(c
         __syncwarp();
     }
     // --- a8: premultiplied RGBA, one 16-byte store ------------------------------
-    if (inside) out[(size_t)y * p.width + x] = make_float4(cr, cg, cb, -expm1f(-tau));
+    if (in_image) out[(size_t)y * p.width + x] = make_float4(cr, cg, cb, -expm1f(-tau));
     if (counter) {
         unsigned long long v = n_look;
 #pragma unroll
@@ -367,6 +390,19 @@ int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
     split_df(prm->t_max_m, &p->tmax_h, &p->tmax_l);
     split_df(1.0 / steps, &p->invn_h, &p->invn_l);
     p->cam_in_layer = cam->pos[2] >= d.slab_lo_m && cam->pos[2] <= d.slab_hi_m;
+    // a ray from below reaches the layer within t_max only if d_z >= (lo - o_z)/t_max
+    p->miss_below = -INFINITY;
+    p->miss_above = INFINITY;
+    if (cam->pos[2] < d.slab_lo_m)
+        p->miss_below = (float)((d.slab_lo_m - cam->pos[2]) / prm->t_max_m * (1.0 - 1e-4) - 1e-6);
+    if (cam->pos[2] > d.slab_hi_m)
+        p->miss_above = (float)(-(cam->pos[2] - d.slab_hi_m) / prm->t_max_m * (1.0 - 1e-4) + 1e-6);
+    p->detail_shift = -1;
+    if (vol->log2_detail) {
+        const double ratio = d.base_period_m / d.detail_period_m;
+        for (int k = 0; k <= 16; ++k)
+            if (ratio == std::ldexp(1.0, k)) p->detail_shift = k;
+    }
     const bool noise = d.density_mode == CLOUD_DENSITY_NOISE;
     const int L[kLatticeAxes] = {vol->log2_base,   vol->log2_base,   vol->log2_base,
                                  vol->log2_detail, vol->log2_detail, vol->log2_detail,
