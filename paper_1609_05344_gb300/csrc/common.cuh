@@ -111,7 +111,7 @@ __device__ __forceinline__ df df_mulf(df a, float b) {
 }
 // 1/b: one Newton step on the FP32 reciprocal.
 __device__ __forceinline__ df df_recip(df b) {
-    const float q = 1.0f / b.hi;
+    const float q = __frcp_rn(b.hi);
     const df p = df_mulf(b, q);                 // b q = 1 - r
     const float r = (1.0f - p.hi) - p.lo;
     return fast_two_sum(q, q * r);
@@ -138,8 +138,7 @@ __device__ __forceinline__ uint32_t int_float_mod32(float v) {
 // round(a) modulo 2^32 (fixed-point wrap) of a double-float; |a| < 2^100.
 __device__ __forceinline__ uint32_t df_to_u32(df a) {
     const float hr = rintf(a.hi);
-    const float rem = rintf((a.hi - hr) + a.lo);
-    return int_float_mod32(hr) + int_float_mod32(rem);
+    return int_float_mod32(hr) + (uint32_t)__float2int_rn((a.hi - hr) + a.lo);
 }
 
 // Host: split an FP64 value into a double-float pair.

@@ -42,7 +42,7 @@ struct MarchParams {
     int32_t h_top;                                       // layer thickness in 2^-16 m
     float h_lo_scale, h_hi_scale;  // 10/thickness, 2.5/thickness, per 2^-16 m
     float sun[3], sun_rad[3], ambient[3];
-    float hg_g, absorption, light_step, tau_max;
+    float hg_g, hg_norm, absorption, light_step, tau_max;  // hg_norm = (1 - g^2)/(4 pi)
     float k0, b_cut, inv_1mc, detail_w, rho0;
     int log2_base, log2_detail, log2_weather;
     int width, height, steps, light_steps, jitter_frame, integration, constant_mode;
@@ -243,9 +243,9 @@ __global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS) march_kernel(c
             Df = D.hi * vlen;
             // --- a5: phase function, hoisted per ray ----------------------------
             const float mu = (v[0].hi * p.sun[0] + v[1].hi * p.sun[1] + v[2].hi * p.sun[2]) * rn.hi;
-            const float g = p.hg_g;
-            const float den = fmaf(-2.0f * g, mu, fmaf(g, g, 1.0f));
-            phase = (1.0f - g * g) / (4.0f * 3.14159265358979f * den * sqrtf(den));
+            // p_HG(mu) = (1 - g^2) / (4 pi) * (1 + g^2 - 2 g mu)^(-3/2)
+            const float r = rsqrtf(fmaf(-2.0f * p.hg_g, mu, fmaf(p.hg_g, p.hg_g, 1.0f)));
+            phase = p.hg_norm * r * r * r;
         }
     }
 #pragma unroll
@@ -432,6 +432,7 @@ int build_params(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
         p->ambient[k] = (float)prm->ambient[k];
     }
     p->hg_g = (float)prm->hg_g;
+    p->hg_norm = (float)((1.0 - prm->hg_g * prm->hg_g) / (4.0 * M_PI));
     p->absorption = (float)prm->absorption_per_m;
     p->light_step = (float)prm->light_step_m;
     p->tau_max = prm->tau_max > 0.0 ? (float)prm->tau_max : INFINITY;
