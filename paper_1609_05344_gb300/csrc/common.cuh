@@ -126,19 +126,15 @@ __device__ __forceinline__ df df_rsqrt(df a) {
 __device__ __forceinline__ bool df_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ df df_max(df a, df b) { return df_gt(a, b) ? a : b; }
 __device__ __forceinline__ df df_min(df a, df b) { return df_gt(a, b) ? b : a; }
-// An integer-valued float modulo 2^32, from its bit pattern (integer ALU
-// only; a 64-bit float-to-integer conversion would use the slow FP64 pipe).
-__device__ __forceinline__ uint32_t int_float_mod32(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xFFu) - 150;  // v = m 2^e, m the 24-bit significand
-    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
-    const uint32_t mag = e >= 0 ? (e < 32 ? m << e : 0u) : (e > -24 ? m >> -e : 0u);
-    return (b >> 31) ? 0u - mag : mag;
-}
-// round(a) modulo 2^32 (fixed-point wrap) of a double-float; |a| < 2^100.
+// round(a) modulo 2^32 (fixed-point wrap) of a double-float with |a| < 2^55:
+// k = round(a.hi / 2^32) and r = a.hi - k 2^32 are exact (|r| <= 2^31, a
+// multiple of ulp(a.hi)); the integer part of r and the rounded remainder
+// (r - round(r)) + a.lo are converted with 32-bit conversions only.
 __device__ __forceinline__ uint32_t df_to_u32(df a) {
-    const float hr = rintf(a.hi);
-    return int_float_mod32(hr) + (uint32_t)__float2int_rn((a.hi - hr) + a.lo);
+    const float k = rintf(a.hi * 2.3283064365386963e-10f);
+    const float r = fmaf(-k, 4294967296.0f, a.hi);
+    const float rr = rintf(r);
+    return (uint32_t)__float2int_rn(rr) + (uint32_t)__float2int_rn((r - rr) + a.lo);
 }
 
 // Host: split an FP64 value into a double-float pair.

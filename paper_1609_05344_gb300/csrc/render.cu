@@ -285,6 +285,10 @@ __global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS) march_kernel(c
             }
             n_look += nA + nlight * __popc(act);
         }
+        if (!__any_sync(kFull, act != 0u)) {
+            // no step of this chunk has density anywhere in the warp
+            continue;
+        }
         // --- B: light marches shared out over the warp (a4, Sec. 1) ----------
         unsigned offs[kChunk + 1];
         offs[0] = 0;
