@@ -159,10 +159,11 @@ inline void split_df10(double v, float *hi, float *lo) {
 // ---------------------------------------------------------------------------
 // Corner-packed tiles.  Record k of an N^3 tile holds the 8 texels of the
 // trilinear footprint whose lowest corner is texel k, with the periodic wrap
-// already applied (corner c = dx + 2 dy + 4 dz); record k of an N^2 tile holds
-// the 4 texels of the bilinear footprint (c = dx + 2 dy).  One lookup is then
-// one contiguous record load (16 B for 16-bit texels, 32 B for FP32) instead
-// of 8 (or 4) scattered texel loads.  Corner 0 of record k is texel k.
+// already applied, in the order r = 4 dx + 2 dy + dz (dz fastest), so that
+// (r, r+1) are the two z-neighbours a packed FP32x2 lerp works on; record k
+// of an N^2 tile holds the 4 texels of the bilinear footprint, r = 2 dx + dy.
+// One lookup is one contiguous record load (16 B for 16-bit texels, 32 B for
+// FP32) instead of 8 (or 4) scattered texel loads.  Texel k is entry 0.
 //
 // The loaders return the corners in an affine "raw" form r = texel + bias so
 // that a 16-bit fixed-point texel decodes with bit operations only; the

@@ -70,18 +70,25 @@ __device__ __forceinline__ uint32_t rec2(int L, uint32_t cx, uint32_t cy) {
     const int sh = 32 - L;
     return ((cy >> sh) << L) | (cx >> sh);
 }
+// Interpolation on packed FP32x2 (Blackwell FFMA2/FADD2): x first on the
+// (z0, z1) pairs of both y rows, then y on the pair, then z.  Each lane of a
+// packed op rounds exactly like the scalar op.
 __device__ __forceinline__ float trilerp(const float c[8], int L, uint32_t cx, uint32_t cy,
                                          uint32_t cz) {
     const float fx = frac23(cx << L), fy = frac23(cy << L), fz = frac23(cz << L);
-    const float c00 = fmaf(fx, c[1] - c[0], c[0]), c10 = fmaf(fx, c[3] - c[2], c[2]);
-    const float c01 = fmaf(fx, c[5] - c[4], c[4]), c11 = fmaf(fx, c[7] - c[6], c[6]);
-    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return fmaf(fz, c1 - c0, c0);
+    const float2 a0 = make_float2(c[0], c[1]), a1 = make_float2(c[2], c[3]);  // dx = 0
+    const float2 b0 = make_float2(c[4], c[5]), b1 = make_float2(c[6], c[7]);  // dx = 1
+    const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
+    const float2 x0 = __ffma2_rn(fx2, __fadd2_rn(b0, make_float2(-a0.x, -a0.y)), a0);  // dy = 0
+    const float2 x1 = __ffma2_rn(fx2, __fadd2_rn(b1, make_float2(-a1.x, -a1.y)), a1);  // dy = 1
+    const float2 yz = __ffma2_rn(fy2, __fadd2_rn(x1, make_float2(-x0.x, -x0.y)), x0);  // (z0, z1)
+    return fmaf(fz, yz.y - yz.x, yz.x);
 }
 __device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, uint32_t cy) {
     const float fx = frac23(cx << L), fy = frac23(cy << L);
-    const float c0 = fmaf(fx, c[1] - c[0], c[0]), c1 = fmaf(fx, c[3] - c[2], c[2]);
-    return fmaf(fy, c1 - c0, c0);
+    const float2 a = make_float2(c[0], c[1]), b = make_float2(c[2], c[3]);  // (y0, y1) at dx
+    const float2 xy = __ffma2_rn(make_float2(fx, fx), __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
+    return fmaf(fy, xy.y - xy.x, xy.x);
 }
 
 // Density at a sample (Sec. 1 "the density is sampled"):

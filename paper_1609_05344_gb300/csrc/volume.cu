@@ -137,10 +137,10 @@ __global__ void pack3_kernel(const T *__restrict__ plain, T *__restrict__ packed
         const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n) & mask,
                        z = (uint32_t)(i >> (2 * log2n));
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint32_t xx = (x + (c & 1)) & mask, yy = (y + ((c >> 1) & 1)) & mask,
-                           zz = (z + (c >> 2)) & mask;
-            packed[8 * i + c] = plain[((uint64_t)zz << (2 * log2n)) | (yy << log2n) | xx];
+        for (int r = 0; r < 8; ++r) {  // r = 4 dx + 2 dy + dz
+            const uint32_t xx = (x + (r >> 2)) & mask, yy = (y + ((r >> 1) & 1)) & mask,
+                           zz = (z + (r & 1)) & mask;
+            packed[8 * i + r] = plain[((uint64_t)zz << (2 * log2n)) | (yy << log2n) | xx];
         }
     }
 }
@@ -153,9 +153,9 @@ __global__ void pack2_kernel(const T *__restrict__ plain, T *__restrict__ packed
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t xx = (x + (c & 1)) & mask, yy = (y + (c >> 1)) & mask;
-            packed[4 * i + c] = plain[(yy << log2n) | xx];
+        for (int r = 0; r < 4; ++r) {  // r = 2 dx + dy
+            const uint32_t xx = (x + (r >> 1)) & mask, yy = (y + (r & 1)) & mask;
+            packed[4 * i + r] = plain[(yy << log2n) | xx];
         }
     }
 }
