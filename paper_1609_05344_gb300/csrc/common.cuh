@@ -173,11 +173,14 @@ __host__ __device__ constexpr float raw_bias() { return 0.0f; }
 template <>
 __host__ __device__ constexpr float raw_bias<uint16_t>() { return 1.5f; }  // 1 + q 2^-16 = v + 1/2 + 1
 
+// An FP32 record is one 32-byte sector, fetched by a single 256-bit load
+// (sm_100+ ld.global .v8): one L1 wavefront instead of two.
 __device__ __forceinline__ void load_rec8(const float *tile, uint32_t rec, float c[8]) {
-    const float4 *p = reinterpret_cast<const float4 *>(tile) + 2 * (size_t)rec;
-    const float4 a = __ldg(p), b = __ldg(p + 1);
-    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
-    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+    const float *p = tile + 8 * (size_t)rec;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]),
+          "=f"(c[7])
+        : "l"(p));
 }
 __device__ __forceinline__ void unpack16(uint32_t w, const __half *, float &lo, float &hi) {
     const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
