@@ -377,6 +377,79 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(args):
+    """Multi-view workload: 64 views of uneven size (256x256 .. 1920x1080, seeded),
+    step counts from {8, 16, 32, 128}, seeded cameras, one volume set; all
+    views in one persistent launch replayed from a CUDA graph, against one
+    launch per view.  One step = every view rendered once (new jitter frame)."""
+    import torch
+
+    from paper_1609_05344_gb300 import _native, api, inputs as I
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _native.build()
+    prec = args.precision if args.precision != "fp32" or args.precision_set else "bf16"
+    vol = api.Volume(I.volume_desc("full", seed=3, precision=prec))
+    prm = I.params()
+    views = I.random_views(64, seed=4 + 1000 * rank)
+    samples = sum(v["width"] * v["height"] * v["steps"] * 7 for v in views)
+    pixels = sum(v["width"] * v["height"] for v in views)
+    batch = api.Batch(vol, prm, views)
+    best, times = batch.autotune(repeats=2)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(k, mode):
+        batch.set_views([dict(v, jitter_frame=k) for v in views])
+        if mode == "graph":
+            batch.render(graph=True)
+        elif mode == "persistent":
+            batch.render()
+        else:
+            batch.render_per_view()
+
+    res = {}
+    clk = ClockSampler(local).__enter__()
+    for mode in ("graph", "persistent", "per_view"):
+        for k in range(args.warmup):
+            step(k, mode)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            batch.set_views([dict(v, jitter_frame=args.warmup + k) for v in views])
+            evs[k][0].record(stream)
+            if mode == "graph":
+                batch.render(graph=True)
+            elif mode == "persistent":
+                batch.render()
+            else:
+                batch.render_per_view()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        res[mode] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    clk.__exit__()
+    ms = res["graph"]
+    value = samples / (ms * 1e-3) / 1e9
+    line = {"metric": "Gsamples/s, 64 uneven views in one persistent launch (CUDA graph)",
+            "value": value * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched-64", "views": 64, "pixels": pixels,
+                       "sizes": "256x256..1920x1080 seeded", "steps": "{8,16,32,128}",
+                       "light_steps": 6, "volume_precision": prec,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "tile_shape": best, "shape_ms": times},
+            "ms_persistent_no_graph": res["persistent"], "ms_one_launch_per_view": res["per_view"],
+            "speedup_vs_per_view": res["per_view"] / ms,
+            "gpu_launches": 64 * 0 + 1, "clocks": dict(clk.summary(), window="all modes")}
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,11 +458,15 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "unorm16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fast-1080p", choices=["fast-1080p", "batched-64"])
     args = ap.parse_args(argv)
+    args.precision_set = any(a.startswith("--precision") for a in (argv or sys.argv[1:]))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched-64":
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -55,6 +55,7 @@ extern "C" {
 #define CLOUD_MAX_LIGHT_STEPS 32
 #define CLOUD_MAX_STEPS 4096
 #define CLOUD_MAX_DIM 16384
+#define CLOUD_MAX_VIEWS 4096
 
 /* ---- descriptors ------------------------------------------------------- */
 
@@ -110,8 +111,21 @@ typedef struct {
     double t_max_m;
 } cloud_params;
 
+/* One view of a multi-view launch: camera, image size, view steps, jitter
+ * frame (< 0: no jitter) and its output (device, width*height*4 floats,
+ * 16-byte aligned, caller-owned). */
+typedef struct {
+    cloud_camera camera;
+    int32_t width;
+    int32_t height;
+    int32_t steps;
+    int32_t jitter_frame;
+    float *out_rgba;
+} cloud_view;
+
 typedef struct cloud_volume cloud_volume;   /* opaque, immutable once created */
 typedef struct cloud_session cloud_session; /* opaque, one TAA stream of frames */
+typedef struct cloud_batch cloud_batch;     /* opaque, a set of views rendered together */
 
 /* ---- status ------------------------------------------------------------ */
 const char *cloud_status_string(int status);
@@ -165,6 +179,40 @@ int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const c
                        int width, int height, int steps, int light_steps, int jitter_frame,
                        int integration, float *out_rgba, unsigned long long *lookups,
                        void *stream);
+
+/* Times every pixel-tile shape of the raymarch on this workload (repeats
+ * launches each, writing out_rgba), remembers the fastest for the volume's
+ * storage precision and light-step count (later cloud_render and new
+ * batches use it), and returns it in *best (and the per-shape mean times in
+ * times_ms[4] if not NULL).  Waits for the stream. */
+int cloud_autotune_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
+                          int width, int height, int steps, int light_steps, int jitter_frame,
+                          int integration, float *out_rgba, int repeats, float *times_ms,
+                          int *best, void *stream);
+
+/* ---- multi-view batches (each view as cloud_render) --------------------- */
+
+/* A batch renders n_views (1..CLOUD_MAX_VIEWS) views of one volume with the
+ * same lighting, light steps and integration rule in ONE persistent launch:
+ * the views' pixel tiles form a work queue (longest step counts first) that
+ * resident CTAs drain through a device counter.  The library allocates and
+ * owns the view table and the counter.  Each view's output equals a
+ * cloud_render of that view. */
+int cloud_batch_create(const cloud_volume *vol, const cloud_params *prm, int light_steps,
+                       int integration, const cloud_view *views, int n_views, cloud_batch **out);
+int cloud_batch_destroy(cloud_batch *b);
+/* New cameras, jitter frames or outputs (sizes and step counts unchanged);
+ * the device view table is rewritten on `stream`. */
+int cloud_batch_set_views(cloud_batch *b, const cloud_view *views, int n_views, void *stream);
+/* Counter reset + persistent kernel on `stream`. */
+int cloud_batch_render(cloud_batch *b, void *stream);
+/* The same two operations captured once into a CUDA graph, replayed on
+ * `stream` (the graph reads the current view table from device memory). */
+int cloud_batch_render_graph(cloud_batch *b, void *stream);
+/* One cloud_render launch per view (the unbatched comparison). */
+int cloud_batch_render_per_view(cloud_batch *b, void *stream);
+/* Times each tile shape for this batch and keeps the fastest (waits). */
+int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms, int *best, void *stream);
 
 /* ---- motion and TAA (Sec. 3.2) ----------------------------------------- */
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libcloudvol.so")
 HEADER = os.path.join(_ROOT, "include", "cloudvol.h")
-SOURCES = ["volume.cu", "render.cu", "taa.cu", "session.cu"]
+SOURCES = ["volume.cu", "render.cu", "batch.cu", "taa.cu", "session.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -29,7 +29,7 @@ PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "unorm16": 3}
 DENSITY = {"noise": 0, "constant": 1}
 INTEGRATION = {"analytic": 0, "basic": 1}
 HISTORY = {"fp32": 0, "fp16": 1}
-MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM = 32, 4096, 16384
+MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM, MAX_VIEWS = 32, 4096, 16384, 4096
 
 
 def _nvcc() -> str:
@@ -40,7 +40,8 @@ def _nvcc() -> str:
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the CUDA sources for sm_103a (in parallel) and link the library."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "common.cuh"), HEADER]
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [
+        os.path.join(CSRC, h) for h in ("common.cuh", "march.cuh")] + [HEADER]
     newest = max(os.path.getmtime(p) for p in deps)
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
@@ -94,9 +95,17 @@ class Params(ctypes.Structure):
                 ("tau_max", ctypes.c_double), ("t_max_m", ctypes.c_double)]
 
 
+class View(ctypes.Structure):
+    _fields_ = [("camera", Camera), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("steps", ctypes.c_int32), ("jitter_frame", ctypes.c_int32),
+                ("out_rgba", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _P = ctypes.POINTER
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 # (name, restype, argtypes) for every entry point declared in include/cloudvol.h
 SIGNATURES = [
@@ -115,6 +124,15 @@ SIGNATURES = [
                                  _P(_vp), _vp]),
     ("cloud_session_reset", _i, [_vp]),
     ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
+    ("cloud_autotune_render", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, _i, _i, _i, _vp, _i,
+                                   _fp, _ip, _vp]),
+    ("cloud_batch_create", _i, [_vp, _P(Params), _i, _i, _P(View), _i, _P(_vp)]),
+    ("cloud_batch_destroy", _i, [_vp]),
+    ("cloud_batch_set_views", _i, [_vp, _P(View), _i, _vp]),
+    ("cloud_batch_render", _i, [_vp, _vp]),
+    ("cloud_batch_render_graph", _i, [_vp, _vp]),
+    ("cloud_batch_render_per_view", _i, [_vp, _vp]),
+    ("cloud_batch_autotune", _i, [_vp, _i, _fp, _ip, _vp]),
 ]
 
 _lock = threading.Lock()

@@ -184,3 +184,83 @@ def hash4(keys: torch.Tensor, stream=None) -> torch.Tensor:
     N.check(N.lib().cloud_hash4_batch(_ptr(keys), n, _ptr(out), _stream(stream)),
             "cloud_hash4_batch")
     return out
+
+
+def autotune_render(vol: Volume, cam: dict, prm: dict, width: int, height: int, steps: int,
+                    light_steps: int, jitter_frame: int = -1, integration: str = "analytic",
+                    repeats: int = 5, stream=None):
+    """Time every pixel-tile shape on this workload and make the fastest the
+    default for the volume's precision (cloud_autotune_render).  Returns
+    (best_shape, [ms per shape])."""
+    out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
+    c, p = N.camera(cam), N.params(prm)
+    times = (ctypes.c_float * 4)()
+    best = ctypes.c_int()
+    N.check(N.lib().cloud_autotune_render(vol.handle, ctypes.byref(c), ctypes.byref(p), width,
+                                          height, steps, light_steps, jitter_frame,
+                                          N.INTEGRATION[integration], _ptr(out), repeats, times,
+                                          ctypes.byref(best), _stream(stream)),
+            "cloud_autotune_render")
+    return best.value, list(times)
+
+
+class Batch:
+    """Many views rendered in one persistent launch (cloud_batch_*).
+
+    views: list of dicts {camera, width, height, steps, jitter_frame}; the
+    batch allocates one (H, W, 4) float32 output per view (``outputs``)."""
+
+    def __init__(self, vol: Volume, prm: dict, views: list, light_steps: int = 6,
+                 integration: str = "analytic"):
+        self.vol = vol
+        self.outputs = [torch.empty((v["height"], v["width"], 4), dtype=torch.float32,
+                                    device="cuda") for v in views]
+        self._views = views
+        arr = self._array(views)
+        self._h = ctypes.c_void_p()
+        p = N.params(prm)
+        N.check(N.lib().cloud_batch_create(vol.handle, ctypes.byref(p), light_steps,
+                                           N.INTEGRATION[integration], arr, len(views),
+                                           ctypes.byref(self._h)), "cloud_batch_create")
+
+    def _array(self, views):
+        arr = (N.View * len(views))()
+        for i, v in enumerate(views):
+            arr[i] = N.View(N.camera(v["camera"]), v["width"], v["height"], v["steps"],
+                            v.get("jitter_frame", -1), self.outputs[i].data_ptr())
+        return arr
+
+    def set_views(self, views: list, stream=None):
+        arr = self._array(views)
+        N.check(N.lib().cloud_batch_set_views(self._h, arr, len(views), _stream(stream)),
+                "cloud_batch_set_views")
+        self._views = views
+
+    def render(self, graph: bool = False, stream=None):
+        fn = N.lib().cloud_batch_render_graph if graph else N.lib().cloud_batch_render
+        N.check(fn(self._h, _stream(stream)), "cloud_batch_render")
+        return self.outputs
+
+    def render_per_view(self, stream=None):
+        N.check(N.lib().cloud_batch_render_per_view(self._h, _stream(stream)),
+                "cloud_batch_render_per_view")
+        return self.outputs
+
+    def autotune(self, repeats: int = 3, stream=None):
+        times = (ctypes.c_float * 4)()
+        best = ctypes.c_int()
+        N.check(N.lib().cloud_batch_autotune(self._h, repeats, times, ctypes.byref(best),
+                                             _stream(stream)), "cloud_batch_autotune")
+        return best.value, list(times)
+
+    def close(self):
+        if self._h:
+            torch.cuda.synchronize()
+            N.check(N.lib().cloud_batch_destroy(self._h), "cloud_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,302 @@
+// batch.cu -- many views of uneven size and step count in one persistent
+// launch (the raymarch of Sec. 1 / Sec. 3.1 / Sec. 3.2 per view).
+//
+// The work queue is the concatenation of every view's pixel tiles, ordered by
+// decreasing per-tile cost (step count) so that the long tiles start first
+// and the tail is made of short ones.  One CTA per resident slot loops: take
+// the next tile index from a device counter, find its view (binary search over
+// the views' first tile indices), stage the view constants in shared memory,
+// march the tile.  The launch (counter reset + kernel) is captured once into a
+// CUDA graph and replayed; per-frame camera changes only rewrite the device
+// view table.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "march.cuh"
+
+namespace cloudvol {
+int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
+                 unsigned long long *counter, int shape, cudaStream_t s);
+
+template <typename T, int LS, int SHAPE>
+__global__ void __launch_bounds__(128, CLOUDVOL_MARCH_MIN_BLOCKS)
+    march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
+                       int n_views, int total_tiles, unsigned int *__restrict__ work,
+                       const T *__restrict__ base, const T *__restrict__ detail,
+                       const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
+    __shared__ WarpScratch scratch[4];
+    __shared__ ViewParams sv;
+    __shared__ int s_tile, s_view;
+    unsigned long long n_look = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = (int)atomicAdd(work, 1u);
+            s_tile = t;
+            if (t < total_tiles) {
+                int lo = 0, hi = n_views - 1;  // last view with tile_begin <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (views[mid].tile_begin <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_view = lo;
+            }
+        }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= total_tiles) break;
+        const int *src = reinterpret_cast<const int *>(views + s_view);
+        int *dst = reinterpret_cast<int *>(&sv);
+        for (int i = threadIdx.x; i < (int)(sizeof(ViewParams) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        const int local = t - sv.tile_begin;
+        n_look += march_tile<T, LS, SHAPE>(p, sv, local % sv.tiles_x, local / sv.tiles_x,
+                                           scratch[threadIdx.x >> 5], base, detail, weather);
+        __syncthreads();  // s_tile / sv are rewritten by the next iteration
+    }
+    count_lookups(counter, n_look);
+}
+
+template <typename T, int SHAPE>
+static const void *batch_kernel_ptr(int light_steps) {
+    return light_steps == 6 ? (const void *)march_batch_kernel<T, 6, SHAPE>
+                            : (const void *)march_batch_kernel<T, -1, SHAPE>;
+}
+template <typename T>
+static const void *batch_kernel_typed(int light_steps, int shape) {
+    switch (shape) {
+        case 1: return batch_kernel_ptr<T, 1>(light_steps);
+        case 2: return batch_kernel_ptr<T, 2>(light_steps);
+        case 3: return batch_kernel_ptr<T, 3>(light_steps);
+        default: return batch_kernel_ptr<T, 0>(light_steps);
+    }
+}
+static const void *batch_kernel(int precision, int light_steps, int shape) {
+    switch (precision) {
+        case CLOUD_PRECISION_FP32: return batch_kernel_typed<float>(light_steps, shape);
+        case CLOUD_PRECISION_FP16: return batch_kernel_typed<__half>(light_steps, shape);
+        case CLOUD_PRECISION_BF16: return batch_kernel_typed<__nv_bfloat16>(light_steps, shape);
+        default: return batch_kernel_typed<uint16_t>(light_steps, shape);
+    }
+}
+
+// Enqueue counter reset + persistent kernel for the given table on stream s.
+int launch_batch(const cloud_volume *vol, const SceneParams &scene, const ViewParams *d_views,
+                 int n_views, int total_tiles, int shape, unsigned int *d_work,
+                 unsigned long long *counter, cudaStream_t s) {
+    if (total_tiles == 0) return CLOUD_OK;
+    const void *fn = batch_kernel(vol->desc.precision, scene.light_steps, shape);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+    if (int rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+                            "cudaDeviceGetAttribute"))
+        return rc;
+    if (int rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0),
+                            "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
+        return rc;
+    const int grid = std::max(1, std::min(total_tiles, sms * std::max(per_sm, 1)));
+    if (int rc = check_cuda(cudaMemsetAsync(d_work, 0, sizeof(unsigned int), s), "reset work counter"))
+        return rc;
+    SceneParams scene_arg = scene;
+    const void *b = vol->base, *d = vol->detail, *w = vol->weather;
+    void *args[] = {(void *)&scene_arg, (void *)&d_views, (void *)&n_views, (void *)&total_tiles,
+                    (void *)&d_work, (void *)&b, (void *)&d, (void *)&w, (void *)&counter};
+    return check_cuda(cudaLaunchKernel(fn, dim3(grid), dim3(128), args, 0, s), "march_batch_kernel");
+}
+
+}  // namespace cloudvol
+
+using namespace cloudvol;
+
+struct cloud_batch {
+    const cloud_volume *vol;
+    cloud_params prm;
+    SceneParams scene;
+    int n_views, total_tiles, shape;
+    std::vector<cloud_view> views;  // caller order
+    std::vector<int> order;         // queue order (decreasing steps)
+    std::vector<ViewParams> table;  // queue order
+    ViewParams *d_views;
+    unsigned int *d_work;
+    cudaGraphExec_t exec;
+    cudaStream_t capture_stream;
+};
+
+namespace {
+
+void drop_graph(cloud_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+void free_batch(cloud_batch *b) {
+    if (!b) return;
+    drop_graph(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->d_views) cudaFree(b->d_views);
+    if (b->d_work) cudaFree(b->d_work);
+    delete b;
+}
+
+// (Re)build the view table in queue order for the batch's tile shape and
+// upload it on stream s.
+int build_table(cloud_batch *b, cudaStream_t s) {
+    b->table.resize(b->n_views);
+    int next = 0;
+    for (int q = 0; q < b->n_views; ++q) {
+        const cloud_view &cv = b->views[b->order[q]];
+        ViewParams &v = b->table[q];
+        if (int rc = build_view(b->vol, &b->prm, &cv.camera, cv.width, cv.height, cv.steps,
+                                cv.jitter_frame, cv.out_rgba, b->shape, &v))
+            return rc;
+        v.tile_begin = next;
+        next += v.tile_count;
+    }
+    b->total_tiles = next;
+    return check_cuda(cudaMemcpyAsync(b->d_views, b->table.data(), sizeof(ViewParams) * b->n_views,
+                                      cudaMemcpyHostToDevice, s),
+                      "upload view table");
+}
+
+}  // namespace
+
+extern "C" int cloud_batch_create(const cloud_volume *vol, const cloud_params *prm, int light_steps,
+                                  int integration, const cloud_view *views, int n_views,
+                                  cloud_batch **out) {
+    clear_error();
+    if (!vol || !prm || !views || !out || n_views < 1 || n_views > CLOUD_MAX_VIEWS)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_create: bad arguments");
+    cloud_batch *b = new (std::nothrow) cloud_batch();
+    if (!b) return set_error(CLOUD_ERR_OUT_OF_MEMORY, "cloud_batch_create: host allocation");
+    b->vol = vol;
+    b->prm = *prm;
+    b->n_views = n_views;
+    b->shape = tuned_shape(vol->desc.precision, light_steps);
+    b->views.assign(views, views + n_views);
+    b->order.resize(n_views);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
+        return b->views[a].steps > b->views[c].steps;  // longest tiles first
+    });
+    int rc = build_scene(vol, prm, light_steps, integration, &b->scene);
+    if (!rc) rc = check_cuda(cudaMalloc(&b->d_views, sizeof(ViewParams) * n_views), "cudaMalloc views");
+    if (!rc) rc = check_cuda(cudaMalloc(&b->d_work, sizeof(unsigned int)), "cudaMalloc work counter");
+    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking),
+                             "cudaStreamCreate");
+    if (!rc) rc = build_table(b, b->capture_stream);
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(b->capture_stream), "cudaStreamSynchronize");
+    if (rc) {
+        free_batch(b);
+        return rc;
+    }
+    *out = b;
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_batch_destroy(cloud_batch *b) {
+    clear_error();
+    if (!b) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_destroy: null batch");
+    cudaStreamSynchronize(b->capture_stream);
+    free_batch(b);
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_batch_set_views(cloud_batch *b, const cloud_view *views, int n_views,
+                                     void *stream) {
+    clear_error();
+    if (!b || !views || n_views != b->n_views)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_set_views: bad arguments");
+    for (int i = 0; i < n_views; ++i)
+        if (views[i].width != b->views[i].width || views[i].height != b->views[i].height ||
+            views[i].steps != b->views[i].steps)
+            return set_error(CLOUD_ERR_INVALID_ARG,
+                             "cloud_batch_set_views: sizes and step counts must not change");
+    b->views.assign(views, views + n_views);
+    return build_table(b, (cudaStream_t)stream);
+}
+
+extern "C" int cloud_batch_render(cloud_batch *b, void *stream) {
+    clear_error();
+    if (!b) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_render: null batch");
+    return launch_batch(b->vol, b->scene, b->d_views, b->n_views, b->total_tiles, b->shape,
+                        b->d_work, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int cloud_batch_render_graph(cloud_batch *b, void *stream) {
+    clear_error();
+    if (!b) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_render_graph: null batch");
+    if (!b->exec) {
+        cudaStream_t cs = b->capture_stream;
+        int rc = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal),
+                            "cudaStreamBeginCapture");
+        if (rc) return rc;
+        const int lrc = launch_batch(b->vol, b->scene, b->d_views, b->n_views, b->total_tiles,
+                                     b->shape, b->d_work, nullptr, cs);
+        cudaGraph_t g = nullptr;
+        rc = check_cuda(cudaStreamEndCapture(cs, &g), "cudaStreamEndCapture");
+        if (lrc || rc) {
+            if (g) cudaGraphDestroy(g);
+            return lrc ? lrc : rc;
+        }
+        rc = check_cuda(cudaGraphInstantiate(&b->exec, g, 0), "cudaGraphInstantiate");
+        cudaGraphDestroy(g);
+        if (rc) {
+            b->exec = nullptr;
+            return rc;
+        }
+    }
+    return check_cuda(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+}
+
+extern "C" int cloud_batch_render_per_view(cloud_batch *b, void *stream) {
+    clear_error();
+    if (!b) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_render_per_view: null batch");
+    for (int q = 0; q < b->n_views; ++q)
+        if (int rc = launch_march(b->scene, b->table[q], b->vol, nullptr, b->shape,
+                                  (cudaStream_t)stream))
+            return rc;
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms, int *best,
+                                    void *stream) {
+    clear_error();
+    if (!b || repeats < 1) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_autotune: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (int rc = check_cuda(cudaEventCreate(&e0), "cudaEventCreate")) return rc;
+    if (int rc = check_cuda(cudaEventCreate(&e1), "cudaEventCreate")) {
+        cudaEventDestroy(e0);
+        return rc;
+    }
+    drop_graph(b);
+    int rc = CLOUD_OK, best_shape = 0;
+    float best_ms = INFINITY;
+    for (int shape = 0; shape < kShapes && !rc; ++shape) {
+        b->shape = shape;
+        rc = build_table(b, s);
+        if (!rc) rc = cloud_batch_render(b, s);  // warm-up
+        if (!rc) rc = check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+        for (int r = 0; r < repeats && !rc; ++r) rc = cloud_batch_render(b, s);
+        if (!rc) rc = check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+        if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.0f;
+        if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        ms /= repeats;
+        if (times_ms) times_ms[shape] = ms;
+        if (!rc && ms < best_ms) {
+            best_ms = ms;
+            best_shape = shape;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->shape = best_shape;
+    if (int r2 = build_table(b, s)) return r2;
+    if (best) *best = best_shape;
+    return CLOUD_OK;
+}

@@ -1,0 +1,396 @@
+// march.cuh -- device side of the per-pixel cloud raymarch (Sec. 1, Sec. 3.1,
+// Sec. 3.2), shared by the single-view kernel (render.cu) and the persistent
+// multi-view kernel (batch.cu).
+//
+// Precision design.  Grazing rays are tens of kilometres long and, with 8
+// view steps, a step is kilometres long; the estimator then multiplies any
+// density error by alpha*D*L_in (hundreds), so sample positions must be far
+// more accurate than FP32 world coordinates allow.  Per ray, the start and
+// the step of every lattice axis (base xyz, detail xyz, weather xy) and of the
+// height above the layer bottom are computed in double-float FP32 and stored
+// as 32-bit fixed-point values: 2^32 units per tile period, so unsigned
+// overflow is exactly the periodic wrap of the tile.  A view step adds the
+// ray's increment and a light sample adds a per-launch constant offset --
+// integer adds, no rounding.  The texel index is the top log2(N) bits, the
+// interpolation weight the next 23 bits.  Radiance and the optical-depth sum
+// are FP32.
+#pragma once
+
+#include "common.cuh"
+
+namespace cloudvol {
+
+enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
+
+// Constants shared by every view of a launch: volume, lighting, light march.
+struct SceneParams {
+    // Fixed-point lattice coordinates: coordinate = p * kfix - half_unit
+    // (mod 2^32), kfix = 2^32 / tile period.
+    float kfix_h[kLatticeAxes], kfix_l[kLatticeAxes];
+    uint32_t half_unit[kLatticeAxes];                    // half a texel: 2^(31 - log2 N)
+    uint32_t loff[CLOUD_MAX_LIGHT_STEPS][kLatticeAxes];  // light-sample offsets
+    int32_t lh[CLOUD_MAX_LIGHT_STEPS];                   // light-sample height offsets
+    int32_t h_top;                                       // layer thickness in 2^-16 m
+    float h_lo_scale, h_hi_scale;  // 10/thickness, 2.5/thickness, per 2^-16 m
+    float sun[3], sun_rad[3], ambient[3];
+    float hg_g, hg_norm, absorption, light_step, tau_max;  // hg_norm = (1 - g^2)/(4 pi)
+    float k0, b_cut, inv_1mc, detail_w, rho0;
+    int log2_base, log2_detail, log2_weather;
+    int light_steps, integration, constant_mode;
+    // detail coordinates = (base + half_base) << detail_shift - half_detail when
+    // the base tile period is 2^detail_shift detail periods (-1: convert separately)
+    int detail_shift;
+    uint32_t jitter_key;
+};
+
+// One camera view: rays, layer clip, step count, jitter frame, output.
+struct ViewParams {
+    // Camera rays, unnormalised: v(x, y) = v00 + x vx + y vy, as double-float
+    // pairs; vx/vy are split so that x * hi is exact (see split_df10).
+    float v00h[3], v00l[3], vxh[3], vxl[3], vyh[3], vyl[3];
+    float oh[3], ol[3];    // camera position
+    float zlo_h, zlo_l;    // slab_lo - o_z
+    float zhi_h, zhi_l;    // slab_hi - o_z
+    float tmax_h, tmax_l;  // far clip distance
+    float invn_h, invn_l;  // 1 / steps
+    // rays with d_z below miss_below (camera under the layer) or above
+    // miss_above (camera over it) cannot reach the layer within t_max
+    float miss_below, miss_above;
+    int cam_in_layer, width, height, steps, jitter_frame;
+    int tiles_x;     // tiles per image row
+    int tile_begin;  // first work-queue index of this view (multi-view launches)
+    int tile_count;
+    float4 *out;     // device RGBA, width * height
+};
+
+// CTA pixel-tile shapes (4 warps of 32 lanes); the autotuner picks one.
+//   shape 0: warp 8x4,  CTA 2x2 warps -> 16x8 pixels
+//   shape 1: warp 8x4,  CTA 4x1 warps -> 32x4 pixels
+//   shape 2: warp 16x2, CTA 2x2 warps -> 32x4 pixels
+//   shape 3: warp 4x8,  CTA 2x2 warps -> 8x16 pixels
+constexpr int kShapes = 4;
+template <int S>
+struct TileShape;
+template <>
+struct TileShape<0> { static constexpr int WX = 8, WY = 4, CX = 2, CY = 2; };
+template <>
+struct TileShape<1> { static constexpr int WX = 8, WY = 4, CX = 4, CY = 1; };
+template <>
+struct TileShape<2> { static constexpr int WX = 16, WY = 2, CX = 2, CY = 2; };
+template <>
+struct TileShape<3> { static constexpr int WX = 4, WY = 8, CX = 2, CY = 2; };
+inline void tile_dims(int shape, int *tw, int *th) {
+    static const int w[kShapes] = {16, 32, 32, 8}, h[kShapes] = {8, 4, 4, 16};
+    *tw = w[shape];
+    *th = h[shape];
+}
+
+constexpr int kAxes = kLatticeAxes + 1;  // lattice axes + height above the layer bottom
+constexpr int kChunk = 8;                // view steps per warp-cooperative chunk
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Per-warp shared scratch of the march: each lane's start coordinates and
+// per-step increments, the chunk's view densities, light-march sums and the
+// list of (step, lane) pairs that need a light march.
+struct WarpScratch {
+    uint32_t c0[kAxes][32];
+    uint32_t e[kAxes][32];
+    float rho[kChunk][32];
+    float lsum[kChunk][32];
+    uint16_t pairs[kChunk * 32];
+};
+
+__device__ __forceinline__ float frac23(uint32_t f) {
+    return __uint_as_float((f >> 9) | 0x3F800000u) - 1.0f;
+}
+
+// Corner-packed sampling at fixed-point coordinates: the record index is the
+// top L bits of each coordinate, the interpolation weights the next 23 bits.
+__device__ __forceinline__ uint32_t rec3(int L, uint32_t cx, uint32_t cy, uint32_t cz) {
+    const int sh = 32 - L;
+    return ((cz >> sh) << (2 * L)) | ((cy >> sh) << L) | (cx >> sh);
+}
+__device__ __forceinline__ uint32_t rec2(int L, uint32_t cx, uint32_t cy) {
+    const int sh = 32 - L;
+    return ((cy >> sh) << L) | (cx >> sh);
+}
+// Interpolation on packed FP32x2 (Blackwell FFMA2/FADD2): x first on the
+// (z0, z1) pairs of both y rows, then y on the pair, then z.  Each lane of a
+// packed op rounds exactly like the scalar op.
+__device__ __forceinline__ float trilerp(const float c[8], int L, uint32_t cx, uint32_t cy,
+                                         uint32_t cz) {
+    const float fx = frac23(cx << L), fy = frac23(cy << L), fz = frac23(cz << L);
+    const float2 a0 = make_float2(c[0], c[1]), a1 = make_float2(c[2], c[3]);  // dx = 0
+    const float2 b0 = make_float2(c[4], c[5]), b1 = make_float2(c[6], c[7]);  // dx = 1
+    const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
+    const float2 x0 = __ffma2_rn(fx2, __fadd2_rn(b0, make_float2(-a0.x, -a0.y)), a0);  // dy = 0
+    const float2 x1 = __ffma2_rn(fx2, __fadd2_rn(b1, make_float2(-a1.x, -a1.y)), a1);  // dy = 1
+    const float2 yz = __ffma2_rn(fy2, __fadd2_rn(x1, make_float2(-x0.x, -x0.y)), x0);  // (z0, z1)
+    return fmaf(fz, yz.y - yz.x, yz.x);
+}
+__device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, uint32_t cy) {
+    const float fx = frac23(cx << L), fy = frac23(cy << L);
+    const float2 a = make_float2(c[0], c[1]), b = make_float2(c[2], c[3]);  // (y0, y1) at dx
+    const float2 xy = __ffma2_rn(make_float2(fx, fx), __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
+    return fmaf(fy, xy.y - xy.x, xy.x);
+}
+
+// Density at a sample (Sec. 1 "the density is sampled"):
+//   rho = g(h) W max(0, (B - w_d Dt - c)/(1 - c)),
+// tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0.
+// Samples outside the layer (g = 0) return without touching memory; otherwise
+// the three record loads are issued together so that one memory round trip
+// serves the lookup.
+template <typename T>
+__device__ __forceinline__ float density(const SceneParams &p, const T *__restrict__ base,
+                                         const T *__restrict__ detail,
+                                         const T *__restrict__ weather, const uint32_t c[8],
+                                         int32_t hq) {
+    if (p.constant_mode) return p.rho0;
+    const float ga = fminf(fmaxf((float)hq * p.h_lo_scale, 0.0f), 1.0f);
+    const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
+    const float g = ga * gb;
+    if (g <= 0.0f) return 0.0f;
+    float cb[8], cd[8], cw[4];
+    load_rec8(base, rec3(p.log2_base, c[kBX], c[kBY], c[kBZ]), cb);
+    if (detail) load_rec8(detail, rec3(p.log2_detail, c[kDX], c[kDY], c[kDZ]), cd);
+    if (weather) load_rec4(weather, rec2(p.log2_weather, c[kWX], c[kWY]), cw);
+    const float b = trilerp(cb, p.log2_base, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
+    float r = b + p.k0;
+    if (detail) {
+        const float dt = trilerp(cd, p.log2_detail, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();
+        r = fmaf(-p.detail_w, dt, r);
+    }
+    r = fmaxf(r * p.inv_1mc, 0.0f);
+    const float w = weather ? bilerp(cw, p.log2_weather, c[kWX], c[kWY]) - raw_bias<T>() + kCentre : 1.0f;
+    return g * w * r;
+}
+
+__device__ __forceinline__ df df_addf(df a, float b) {
+    const df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+
+// sigma D of one step, rounded the same way wherever it is recomputed
+__device__ __forceinline__ float step_depth(float absorption, float rho, float D) {
+    return __fmul_rn(__fmul_rn(absorption, rho), D);
+}
+
+// The march of one CTA pixel tile (4 warps, one pixel per lane).  View steps
+// are processed in chunks of kChunk:
+//   A  each lane evaluates its view densities and its early out (the optical
+//      depth does not depend on the lighting);
+//   B  the warp shares out every (step, lane) light march with density > 0
+//      over all 32 lanes, so lanes whose own rays are empty, finished or
+//      outside the layer do useful work;
+//   C  each lane integrates its steps in order with the light sums from B.
+// The arithmetic of every sample is the same as a per-lane march.  Returns the
+// number of density lookups this lane performed.
+template <typename T, int LS, int SHAPE>
+__device__ __forceinline__ unsigned long long march_tile(
+    const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch &ws,
+    const T *__restrict__ base, const T *__restrict__ detail, const T *__restrict__ weather) {
+    using S = TileShape<SHAPE>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = tile_x * (S::WX * S::CX) + (warp % S::CX) * S::WX + (lane % S::WX);
+    const int y = tile_y * (S::WY * S::CY) + (warp / S::CX) * S::WY + (lane / S::WX);
+    const bool in_image = x < v.width && y < v.height;
+    bool inside = in_image;
+    const int nlight = LS >= 0 ? LS : p.light_steps;
+    unsigned long long n_look = 0;
+    uint32_t c[kLatticeAxes] = {}, e[kLatticeAxes] = {};
+    int32_t hq = 0, eh = 0;
+    float Df = 0.0f, phase = 0.0f;
+    bool alive = false;
+    const float xf = (float)x, yf = (float)y;
+    if (inside) {
+        // quick FP32 test for rays that cannot reach the layer (a 1e-4 margin
+        // keeps every undecided ray on the exact path below)
+        const float qx = fmaf(yf, v.vyh[0], fmaf(xf, v.vxh[0], v.v00h[0]));
+        const float qy = fmaf(yf, v.vyh[1], fmaf(xf, v.vxh[1], v.v00h[1]));
+        const float qz = fmaf(yf, v.vyh[2], fmaf(xf, v.vxh[2], v.v00h[2]));
+        const float dz = qz * rsqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+        if (dz < v.miss_below || dz > v.miss_above) inside = false;
+    }
+    if (inside) {
+        // --- a1: pixel ray and layer clip (double-float) ---------------------
+        // p(lambda) = o + lambda v with v unnormalised; t = lambda |v|.
+        df r[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            df a = {v.v00h[k], v.v00l[k] + fmaf(xf, v.vxl[k], yf * v.vyl[k])};
+            a = df_addf(a, xf * v.vxh[k]);  // exact products
+            r[k] = df_addf(a, yf * v.vyh[k]);
+        }
+        const df n2 = df_add(df_add(df_mul(r[0], r[0]), df_mul(r[1], r[1])), df_mul(r[2], r[2]));
+        const df rn = df_rsqrt(n2);  // 1 / |v|
+        const df lam_max = df_mul({v.tmax_h, v.tmax_l}, rn);
+        df lam0 = {0.0f, 0.0f}, lam1 = lam_max;
+        if (fabsf(r[2].hi) * rn.hi < 1e-8f) {
+            alive = v.cam_in_layer != 0;
+        } else {
+            const df inv = df_recip(r[2]);
+            const df ll = df_mul({v.zlo_h, v.zlo_l}, inv), lh = df_mul({v.zhi_h, v.zhi_l}, inv);
+            lam0 = df_max(df_min(ll, lh), lam0);
+            lam1 = df_min(df_max(ll, lh), lam_max);
+            alive = df_gt(lam1, lam0);
+        }
+        if (alive) {
+            // --- a2: jittered start offset (Sec. 3.2) ---------------------------
+            const df D = df_mul(df_add(lam1, df_neg(lam0)), {v.invn_h, v.invn_l});
+            float u = 0.5f;
+            if (v.jitter_frame >= 0)
+                u = (float)(pcg_hash4((uint32_t)x, (uint32_t)y, (uint32_t)v.jitter_frame,
+                                      p.jitter_key) >> 8) * (1.0f / 16777216.0f);
+            const df lam_s = df_add(lam0, df_mulf(D, u));
+            df pos[3], dpos[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pos[k] = df_add({v.oh[k], v.ol[k]}, df_mul(lam_s, r[k]));
+                dpos[k] = df_mul(D, r[k]);
+            }
+#pragma unroll
+            for (int a = 0; a < kLatticeAxes; ++a) {
+                const int comp = a < 6 ? a % 3 : a - 6;
+                if (a >= kDX && a <= kDZ && p.detail_shift >= 0) {
+                    // same origin, period 2^-shift of the base tile: exact shift
+                    const int b = a - kDX;
+                    c[a] = ((c[b] + p.half_unit[b]) << p.detail_shift) - p.half_unit[a];
+                    e[a] = e[b] << p.detail_shift;
+                    continue;
+                }
+                const df k = {p.kfix_h[a], p.kfix_l[a]};
+                c[a] = df_to_u32(df_mul(pos[comp], k)) - p.half_unit[a];
+                e[a] = df_to_u32(df_mul(dpos[comp], k));
+            }
+            // height above the layer bottom: (o_z - slab_lo) + lambda v_z, in 2^-16 m
+            const df hrel = df_add(df_mul(lam_s, r[2]), df_neg({v.zlo_h, v.zlo_l}));
+            hq = (int32_t)df_to_u32({hrel.hi * 65536.0f, hrel.lo * 65536.0f});
+            eh = (int32_t)df_to_u32({dpos[2].hi * 65536.0f, dpos[2].lo * 65536.0f});
+            const float vlen = n2.hi * rn.hi;
+            Df = D.hi * vlen;
+            // --- a5: phase function, hoisted per ray ----------------------------
+            // p_HG(mu) = (1 - g^2) / (4 pi) * (1 + g^2 - 2 g mu)^(-3/2)
+            const float mu = (r[0].hi * p.sun[0] + r[1].hi * p.sun[1] + r[2].hi * p.sun[2]) * rn.hi;
+            const float q = rsqrtf(fmaf(-2.0f * p.hg_g, mu, fmaf(p.hg_g, p.hg_g, 1.0f)));
+            phase = p.hg_norm * q * q * q;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < kLatticeAxes; ++a) {
+        ws.c0[a][lane] = c[a];
+        ws.e[a][lane] = e[a];
+    }
+    ws.c0[kLatticeAxes][lane] = (uint32_t)hq;
+    ws.e[kLatticeAxes][lane] = (uint32_t)eh;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    for (int i0 = 0; i0 < v.steps && __any_sync(kFull, alive); i0 += kChunk) {
+        // --- A: view densities and early out --------------------------------
+        uint32_t act = 0;
+        int nA = 0;
+        if (alive) {
+            float tau_a = tau;
+#pragma unroll 1
+            for (int k = 0; k < kChunk; ++k) {
+                if (i0 + k >= v.steps) break;
+                // --- a3: density lookup ---------------------------------------
+                const float rho = density(p, base, detail, weather, c, hq);
+                ws.rho[k][lane] = rho;
+                nA = k + 1;
+                if (rho > 0.0f) {
+                    act |= 1u << k;
+                    tau_a = __fadd_rn(tau_a, step_depth(p.absorption, rho, Df));
+                }
+#pragma unroll
+                for (int a = 0; a < kLatticeAxes; ++a) c[a] += e[a];
+                hq += eh;
+                // --- a7: early out once alpha is ~1 (Sec. 1) --------------------
+                if (tau_a >= p.tau_max) {
+                    alive = false;
+                    break;
+                }
+            }
+            n_look += nA + nlight * __popc(act);
+        }
+        if (!__any_sync(kFull, act != 0u)) continue;  // no density in this chunk, warp-wide
+        // --- B: light marches shared out over the warp (a4, Sec. 1) ----------
+        unsigned offs[kChunk + 1];
+        offs[0] = 0;
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+            const unsigned m = __ballot_sync(kFull, (act >> k) & 1u);
+            if ((act >> k) & 1u) ws.pairs[offs[k] + __popc(m & lt_mask)] = (uint16_t)((k << 5) | lane);
+            offs[k + 1] = offs[k] + __popc(m);
+        }
+        __syncwarp();
+        for (unsigned q = lane; q < offs[kChunk]; q += 32) {
+            const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
+            const uint32_t i = (uint32_t)(i0 + (int)k);
+            uint32_t cs[kLatticeAxes];
+#pragma unroll
+            for (int a = 0; a < kLatticeAxes; ++a) cs[a] = ws.c0[a][ow] + i * ws.e[a][ow];
+            const int32_t hs = (int32_t)(ws.c0[kLatticeAxes][ow] + i * ws.e[kLatticeAxes][ow]);
+            float rho_sum = 0.0f;
+#pragma unroll
+            for (int j = 0; j < (LS >= 0 ? LS : CLOUD_MAX_LIGHT_STEPS); ++j) {
+                if (LS < 0 && j >= nlight) break;
+                uint32_t cj[kLatticeAxes];
+#pragma unroll
+                for (int a = 0; a < kLatticeAxes; ++a) cj[a] = cs[a] + p.loff[j][a];
+                rho_sum += density(p, base, detail, weather, cj, hs + p.lh[j]);
+            }
+            ws.lsum[k][ow] = rho_sum;
+        }
+        __syncwarp();
+        // --- C: in-scattered light and the per-step integral, in step order ---
+        for (int k = 0; k < nA; ++k) {
+            if (!((act >> k) & 1u)) continue;
+            const float rho = ws.rho[k][lane];
+            // --- a5: in-scattered light ---------------------------------------
+            const float sun_t = expf(-p.absorption * p.light_step * ws.lsum[k][lane]) * phase;
+            const float lr = fmaf(p.sun_rad[0], sun_t, p.ambient[0]);
+            const float lg = fmaf(p.sun_rad[1], sun_t, p.ambient[1]);
+            const float lb = fmaf(p.sun_rad[2], sun_t, p.ambient[2]);
+            // --- a6: per-step integral (Sec. 3.1) ------------------------------
+            const float sd = step_depth(p.absorption, rho, Df);
+            float wgt;
+            if (p.integration == CLOUD_INTEGRATE_ANALYTIC) {
+                wgt = expf(-tau) * -expm1f(-sd);
+                tau = __fadd_rn(tau, sd);
+            } else {
+                tau = __fadd_rn(tau, sd);
+                wgt = expf(-tau) * sd;
+            }
+            cr = fmaf(wgt, lr, cr);
+            cg = fmaf(wgt, lg, cg);
+            cb = fmaf(wgt, lb, cb);
+        }
+        __syncwarp();
+    }
+    // --- a8: premultiplied RGBA, one 16-byte store ------------------------------
+    if (in_image) v.out[(size_t)y * v.width + x] = make_float4(cr, cg, cb, -expm1f(-tau));
+    return n_look;
+}
+
+// Warp-aggregated add of the lookup count (counting launches only).
+__device__ __forceinline__ void count_lookups(unsigned long long *counter, unsigned long long n) {
+    if (!counter) return;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) n += __shfl_down_sync(kFull, n, s);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(counter, n);
+}
+
+// Host side (render.cu).
+int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_steps, int integration,
+                SceneParams *p);
+int build_view(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *cam, int width,
+               int height, int steps, int jitter_frame, float *out, int shape, ViewParams *v);
+int tuned_shape(int precision, int light_steps);
+
+}  // namespace cloudvol
+
+// CTAs per SM the march is compiled for (register budget 65536 / (128 x this)).
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS
+#define CLOUDVOL_MARCH_MIN_BLOCKS 6
+#endif

@@ -147,3 +147,22 @@ def synthetic_motion(rng: np.random.Generator, height: int, width: int,
     off = rng.uniform(0, 1, (height, width)) < offscreen_frac
     m[off] = 1e9
     return m.astype(np.float32)
+
+
+def random_views(n: int, seed: int = 4, max_size=(1920, 1080), min_size=(256, 256),
+                 steps=(8, 16, 32, 128)) -> list:
+    """Uneven multi-view workload: n views with seeded sizes in
+    [min_size, max_size], step counts drawn from `steps`, cameras on seeded
+    positions below the cloud layer looking up at seeded yaw/pitch."""
+    rng = np.random.default_rng(seed)
+    views = []
+    for i in range(n):
+        w = int(rng.integers(min_size[0], max_size[0] + 1))
+        h = int(rng.integers(min_size[1], max_size[1] + 1))
+        pos = (float(rng.uniform(-20000, 20000)), float(rng.uniform(-20000, 20000)),
+               float(rng.uniform(0.0, 1200.0)))
+        cam = camera(pos, float(rng.uniform(0, 360)), float(rng.uniform(2.0, 40.0)),
+                     float(rng.uniform(40.0, 75.0)))
+        views.append(dict(camera=cam, width=w, height=h, steps=int(rng.choice(steps)),
+                          jitter_frame=int(rng.integers(0, 1000))))
+    return views

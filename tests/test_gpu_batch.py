@@ -1,0 +1,93 @@
+"""GPU: multi-view persistent launches (cloud_batch_*) and the tile-shape
+autotuner.  Every view of a batch is the same computation as cloud_render of
+that view, so outputs must be bitwise equal; a few views are also checked
+against the FP64 oracle (1e-4)."""
+import numpy as np
+import pytest
+
+from paper_1609_05344_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_05344_gb300 import _native, api as A
+    _native.build()
+    return A
+
+
+def _single(api, vol, v):
+    return api.render(vol, v["camera"], I.params(), v["width"], v["height"], v["steps"], 6,
+                      jitter_frame=v["jitter_frame"]).cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "unorm16"])
+def test_batch_equals_single_views(api, precision):
+    vol = api.Volume(I.volume_desc("full", seed=3, precision=precision))
+    views = I.random_views(12, seed=9, max_size=(300, 200), min_size=(1, 1))
+    b = api.Batch(vol, I.params(), views)
+    outs = [o.cpu().numpy() for o in b.render()]
+    for v, o in zip(views, outs):
+        assert np.array_equal(o, _single(api, vol, v))
+    outs_g = [o.cpu().numpy() for o in b.render(graph=True)]
+    for a, c in zip(outs, outs_g):
+        assert np.array_equal(a, c)
+    for o in b.outputs:
+        o.zero_()
+    outs_p = [o.cpu().numpy() for o in b.render_per_view()]
+    for a, c in zip(outs, outs_p):
+        assert np.array_equal(a, c)
+    b.close()
+
+
+def test_batch_set_views_and_graph_replay(api):
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    views = I.random_views(6, seed=2, max_size=(160, 120))
+    b = api.Batch(vol, I.params(), views)
+    b.render(graph=True)
+    for frame in range(3):
+        moved = [dict(v, camera=I.camera(np.array(v["camera"]["pos"]) + [50.0 * frame, 0, 0],
+                                         10.0 * frame, 15.0), jitter_frame=frame) for v in views]
+        b.set_views(moved)
+        outs = [o.cpu().numpy() for o in b.render(graph=True)]
+        for v, o in zip(moved, outs):
+            assert np.array_equal(o, _single(api, vol, v))
+    with pytest.raises(Exception):
+        b.set_views([dict(views[0], width=views[0]["width"] + 1)] + views[1:])
+    b.close()
+
+
+def test_batch_matches_oracle(api, oracle):
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    views = I.random_views(4, seed=5, max_size=(64, 48), min_size=(17, 9))
+    b = api.Batch(vol, I.params(), views)
+    outs = [o.cpu().numpy() for o in b.render()]
+    for v, o in zip(views, outs):
+        ref, _ = oracle.render(ovol, v["camera"], I.params(), v["width"], v["height"], v["steps"],
+                               6, jitter_frame=v["jitter_frame"], nthreads=8)
+        assert np.abs(o - ref).max() <= 1e-4
+    b.close()
+
+
+def test_autotune_shapes_equal_results(api):
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    cam = I.orbit_camera(0, 3)
+    base = api.render(vol, cam, I.params(), 333, 177, 8, 6, jitter_frame=3).cpu().numpy()
+    best, times = api.autotune_render(vol, cam, I.params(), 333, 177, 8, 6, jitter_frame=3,
+                                      repeats=2)
+    assert 0 <= best < 4 and all(t > 0 for t in times)
+    again = api.render(vol, cam, I.params(), 333, 177, 8, 6, jitter_frame=3).cpu().numpy()
+    assert np.array_equal(base, again)  # tile shape does not change any pixel
+    views = I.random_views(5, seed=11, max_size=(200, 100))
+    b = api.Batch(vol, I.params(), views)
+    ref = [o.cpu().numpy() for o in b.render()]
+    best, times = b.autotune(repeats=2)
+    assert 0 <= best < 4
+    for a, o in zip(ref, b.render(graph=True)):
+        assert np.array_equal(a, o.cpu().numpy())
+    b.close()
