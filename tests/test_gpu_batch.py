@@ -46,7 +46,7 @@ def test_batch_equals_single_views(api, precision):
 
 def test_batch_set_views_and_graph_replay(api):
     vol = api.Volume(I.volume_desc("full", seed=3))
-    views = I.random_views(6, seed=2, max_size=(160, 120))
+    views = I.random_views(6, seed=2, max_size=(160, 120), min_size=(8, 8))
     b = api.Batch(vol, I.params(), views)
     b.render(graph=True)
     for frame in range(3):
@@ -83,7 +83,7 @@ def test_autotune_shapes_equal_results(api):
     assert 0 <= best < 4 and all(t > 0 for t in times)
     again = api.render(vol, cam, I.params(), 333, 177, 8, 6, jitter_frame=3).cpu().numpy()
     assert np.array_equal(base, again)  # tile shape does not change any pixel
-    views = I.random_views(5, seed=11, max_size=(200, 100))
+    views = I.random_views(5, seed=11, max_size=(200, 100), min_size=(8, 8))
     b = api.Batch(vol, I.params(), views)
     ref = [o.cpu().numpy() for o in b.render()]
     best, times = b.autotune(repeats=2)
