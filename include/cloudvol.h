@@ -56,6 +56,7 @@ extern "C" {
 #define CLOUD_MAX_STEPS 4096
 #define CLOUD_MAX_DIM 16384
 #define CLOUD_MAX_VIEWS 4096
+#define CLOUD_STATIC_MAX_VIEWS 256
 
 /* ---- descriptors ------------------------------------------------------- */
 
@@ -213,6 +214,24 @@ int cloud_batch_render_graph(cloud_batch *b, void *stream);
 int cloud_batch_render_per_view(cloud_batch *b, void *stream);
 /* Times each tile shape for this batch and keeps the fastest (waits). */
 int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms, int *best, void *stream);
+
+/* Renders n_views views exactly as cloud_batch_create + cloud_batch_render
+ * would, but allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library call.  The paper has no counterpart to this entry point; it is for
+ * callers that cannot allocate device memory at render time, such as a
+ * real-time render thread or an engine with a fixed device-memory budget,
+ * where cudaMalloc/cudaFree may block, synchronize the device or fail.
+ * The caller still owns every view's out_rgba.  The scratch (work counter and
+ * view table) is one library-wide static device array sized for
+ * CLOUD_STATIC_MAX_VIEWS (256) views, 45312 bytes, which every GPU that loads
+ * the library holds until the process exits; n_views above 256 returns
+ * CLOUD_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address (a runtime query), so make it before any stream capture.
+ * Every call reuses the same array and resets the counter itself; calls whose
+ * work overlaps on the GPU (e.g. on two streams) race on it, so issue them on
+ * one stream or otherwise order them. */
+int cloud_batch_render_static(const cloud_volume *vol, const cloud_params *prm, int light_steps,
+                              int integration, const cloud_view *views, int n_views, void *stream);
 
 /* ---- motion and TAA (Sec. 3.2) ----------------------------------------- */
 

@@ -29,7 +29,7 @@ PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "unorm16": 3}
 DENSITY = {"noise": 0, "constant": 1}
 INTEGRATION = {"analytic": 0, "basic": 1}
 HISTORY = {"fp32": 0, "fp16": 1}
-MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM, MAX_VIEWS = 32, 4096, 16384, 4096
+MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM, MAX_VIEWS, STATIC_MAX_VIEWS = 32, 4096, 16384, 4096, 256
 
 
 def _nvcc() -> str:
@@ -133,6 +133,7 @@ SIGNATURES = [
     ("cloud_batch_render_graph", _i, [_vp, _vp]),
     ("cloud_batch_render_per_view", _i, [_vp, _vp]),
     ("cloud_batch_autotune", _i, [_vp, _i, _fp, _ip, _vp]),
+    ("cloud_batch_render_static", _i, [_vp, _P(Params), _i, _i, _P(View), _i, _vp]),
 ]
 
 _lock = threading.Lock()

@@ -11,6 +11,7 @@
 // view table.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -299,4 +300,77 @@ extern "C" int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms
     if (int r2 = build_table(b, s)) return r2;
     if (best) *best = best_shape;
     return CLOUD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the multi-view launch.  Its scratch (the work
+// counter and the view table) lives in one file-scope device array sized for
+// CLOUD_STATIC_MAX_VIEWS views, which every GPU that loads the library keeps
+// until the process exits.  Host code cannot pass the array's name to a
+// kernel (on the host it only stands in for the symbol), so the device address
+// is looked up once per device with that device current and cached.
+namespace {
+constexpr size_t kStaticTableOffset = 256;  // the counter sits in the first 256 bytes
+constexpr size_t kStaticBytes = kStaticTableOffset + sizeof(ViewParams) * CLOUD_STATIC_MAX_VIEWS;
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+static int static_scratch_address(void **out) {
+    int dev = 0;
+    if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(CLOUD_ERR_UNSUPPORTED, "cloud_batch_render_static: device index >= 64");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        if (int rc = check_cuda(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress"))
+            return rc;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_batch_render_static(const cloud_volume *vol, const cloud_params *prm,
+                                         int light_steps, int integration, const cloud_view *views,
+                                         int n_views, void *stream) {
+    clear_error();
+    if (!vol || !prm || !views || n_views < 1)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_render_static: bad arguments");
+    if (n_views > CLOUD_STATIC_MAX_VIEWS)
+        return set_error(CLOUD_ERR_INVALID_ARG,
+                         "cloud_batch_render_static: more views than the static scratch holds (256)");
+    SceneParams scene;
+    if (int rc = build_scene(vol, prm, light_steps, integration, &scene)) return rc;
+    // host staging of the table: per-thread static storage, no per-call allocation
+    thread_local ViewParams table[CLOUD_STATIC_MAX_VIEWS];
+    int order[CLOUD_STATIC_MAX_VIEWS];
+    for (int i = 0; i < n_views; ++i) order[i] = i;
+    for (int i = 1; i < n_views; ++i)  // stable insertion sort, longest step counts first
+        for (int j = i; j > 0 && views[order[j]].steps > views[order[j - 1]].steps; --j)
+            std::swap(order[j], order[j - 1]);
+    const int shape = tuned_shape(vol->desc.precision, light_steps);
+    int next = 0;
+    for (int q = 0; q < n_views; ++q) {
+        const cloud_view &cv = views[order[q]];
+        if (int rc = build_view(vol, prm, &cv.camera, cv.width, cv.height, cv.steps, cv.jitter_frame,
+                                cv.out_rgba, shape, &table[q]))
+            return rc;
+        table[q].tile_begin = next;
+        next += table[q].tile_count;
+    }
+    void *base = nullptr;
+    if (int rc = static_scratch_address(&base)) return rc;
+    unsigned int *work = static_cast<unsigned int *>(base);
+    ViewParams *d_views = reinterpret_cast<ViewParams *>(static_cast<char *>(base) + kStaticTableOffset);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = check_cuda(cudaMemcpyAsync(d_views, table, sizeof(ViewParams) * n_views,
+                                            cudaMemcpyHostToDevice, s),
+                            "cloud_batch_render_static: upload view table"))
+        return rc;
+    return launch_batch(vol, scene, d_views, n_views, next, shape, work, nullptr, s);
 }
