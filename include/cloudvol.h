@@ -127,6 +127,36 @@ typedef struct {
 typedef struct cloud_volume cloud_volume;   /* opaque, immutable once created */
 typedef struct cloud_session cloud_session; /* opaque, one TAA stream of frames */
 typedef struct cloud_batch cloud_batch;     /* opaque, a set of views rendered together */
+typedef struct cloud_server cloud_server;   /* opaque, continuous-batching render server */
+
+/* Render server configuration. */
+typedef struct {
+    int32_t max_batch_views; /* requests per batch, 1..CLOUD_MAX_VIEWS (1 = a launch per frame) */
+    int32_t slots;           /* batches in flight at once (one stream each), 1..8 */
+    int32_t max_sessions;    /* session table size, 1..65536 */
+    int32_t history_fmt;     /* CLOUD_HISTORY_* */
+    float blend;             /* TAA blend, [0, 1] */
+    uint64_t reserve_bytes;  /* device memory left free when admitting a session */
+    uint64_t budget_bytes;   /* 0: none; else the most all sessions may hold */
+} cloud_server_config;
+
+/* Per-request timing returned by cloud_server_wait. */
+typedef struct {
+    int32_t session;
+    int32_t steps;
+    int32_t batch_size; /* requests in the batch that carried it */
+    double queue_ms;    /* submit -> batch launch */
+    double latency_ms;  /* submit -> device work complete */
+} cloud_request_info;
+
+typedef struct {
+    uint64_t completed;
+    uint64_t batches;
+    uint64_t batched_views;
+    uint64_t queued;
+    int32_t open_sessions;
+    uint64_t session_bytes;
+} cloud_server_counters;
 
 /* ---- status ------------------------------------------------------------ */
 const char *cloud_status_string(int status);
@@ -278,6 +308,47 @@ int cloud_session_frame(cloud_session *s, const cloud_camera *cam, const cloud_p
 
 /* Forgets the history: the next frame is a first frame (index kept). */
 int cloud_session_reset(cloud_session *s);
+
+/* ---- continuous-batching render server ----------------------------------- */
+
+/* A server renders TAA frames (as cloud_session_frame, Sec. 3.2) for many
+ * sessions of one volume.  A worker thread forms batches from the request
+ * queue whenever an in-flight slot is free: in arrival order, at most one
+ * request per session (its next frame needs the history of the previous one)
+ * and at most max_batch_views requests; a batch is one persistent raymarch
+ * over its views plus each request's motion and TAA resolve on the slot's
+ * stream, so with slots > 1 batches overlap on the device.  Requests that
+ * arrive while batches run join the next batch.  Each session's result is
+ * the same whether it is rendered alone or among others.  The library
+ * allocates and owns all buffers. */
+int cloud_server_create(const cloud_volume *vol, const cloud_params *prm, int light_steps,
+                        const cloud_server_config *cfg, cloud_server **out);
+/* Stops the worker, waits for in-flight batches, frees everything. */
+int cloud_server_destroy(cloud_server *srv);
+/* Admits a session of width x height if the free device memory minus its
+ * buffers stays above reserve_bytes and the budget allows it
+ * (CLOUD_ERR_OUT_OF_MEMORY otherwise).  Its history, raw frame, motion and
+ * jitter index live on the device. */
+int cloud_server_open_session(cloud_server *srv, int width, int height, int *session_id);
+/* Frees a session with no queued request; waits (at most 10 s) for an
+ * in-flight frame. */
+int cloud_server_close_session(cloud_server *srv, int session_id);
+/* Queues the next frame of a session (camera, view steps); returns at once. */
+int cloud_server_submit(cloud_server *srv, int session_id, const cloud_camera *cam, int steps,
+                        uint64_t *ticket);
+/* Waits at most timeout_ms for a request (CLOUD_ERR_TIMEOUT otherwise), then
+ * returns its timing and forgets the ticket. */
+int cloud_server_wait(cloud_server *srv, uint64_t ticket, int timeout_ms, cloud_request_info *info);
+/* Device address of a session's latest resolved frame (history format),
+ * NULL before its first frame; invalid while a frame of it is in flight. */
+int cloud_server_session_output(cloud_server *srv, int session_id, const void **dev_out);
+/* Copies a session's latest resolved frame (width*height*4 values of the
+ * history format, `bytes` must match) to dst (host or device); waits. */
+int cloud_server_copy_output(cloud_server *srv, int session_id, void *dst, size_t bytes);
+/* Holds (paused != 0) or releases batch formation; queued requests wait. */
+int cloud_server_pause(cloud_server *srv, int paused);
+/* Counters; returns the server's sticky error status (CLOUD_OK if none). */
+int cloud_server_stats(cloud_server *srv, cloud_server_counters *st);
 
 /* ---- test hooks -------------------------------------------------------- */
 

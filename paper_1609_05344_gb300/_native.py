@@ -17,7 +17,7 @@ CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libcloudvol.so")
 HEADER = os.path.join(_ROOT, "include", "cloudvol.h")
-SOURCES = ["volume.cu", "render.cu", "batch.cu", "taa.cu", "session.cu"]
+SOURCES = ["volume.cu", "render.cu", "batch.cu", "taa.cu", "session.cu", "server.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -101,6 +101,25 @@ class View(ctypes.Structure):
                 ("out_rgba", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch_views", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("max_sessions", ctypes.c_int32), ("history_fmt", ctypes.c_int32),
+                ("blend", ctypes.c_float), ("reserve_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("batched_views", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("open_sessions", ctypes.c_int32), ("session_bytes", ctypes.c_uint64)]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _P = ctypes.POINTER
@@ -134,6 +153,16 @@ SIGNATURES = [
     ("cloud_batch_render_per_view", _i, [_vp, _vp]),
     ("cloud_batch_autotune", _i, [_vp, _i, _fp, _ip, _vp]),
     ("cloud_batch_render_static", _i, [_vp, _P(Params), _i, _i, _P(View), _i, _vp]),
+    ("cloud_server_create", _i, [_vp, _P(Params), _i, _P(ServerConfig), _P(_vp)]),
+    ("cloud_server_destroy", _i, [_vp]),
+    ("cloud_server_open_session", _i, [_vp, _i, _i, _ip]),
+    ("cloud_server_close_session", _i, [_vp, _i]),
+    ("cloud_server_submit", _i, [_vp, _i, _P(Camera), _i, _P(ctypes.c_uint64)]),
+    ("cloud_server_wait", _i, [_vp, ctypes.c_uint64, _i, _P(RequestInfo)]),
+    ("cloud_server_session_output", _i, [_vp, _i, _P(_vp)]),
+    ("cloud_server_copy_output", _i, [_vp, _i, _vp, ctypes.c_size_t]),
+    ("cloud_server_pause", _i, [_vp, _i]),
+    ("cloud_server_stats", _i, [_vp, _P(ServerCounters)]),
 ]
 
 _lock = threading.Lock()

@@ -264,3 +264,77 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching render server (cloud_server_*): many TAA sessions of
+    one volume, frames batched into persistent launches as they arrive."""
+
+    def __init__(self, vol: Volume, prm: dict, light_steps: int = 6, max_batch_views: int = 64,
+                 slots: int = 2, max_sessions: int = 512, history_fmt: str = "fp16",
+                 blend: float = 0.1, reserve_bytes: int = 1 << 30, budget_bytes: int = 0):
+        self.vol, self.history_fmt = vol, history_fmt
+        cfg = N.ServerConfig(max_batch_views, slots, max_sessions, N.HISTORY[history_fmt],
+                             float(blend), reserve_bytes, budget_bytes)
+        p = N.params(prm)
+        self._h = ctypes.c_void_p()
+        N.check(N.lib().cloud_server_create(vol.handle, ctypes.byref(p), light_steps,
+                                            ctypes.byref(cfg), ctypes.byref(self._h)),
+                "cloud_server_create")
+        self.sizes = {}
+
+    def open_session(self, width: int, height: int) -> int:
+        sid = ctypes.c_int()
+        N.check(N.lib().cloud_server_open_session(self._h, width, height, ctypes.byref(sid)),
+                "cloud_server_open_session")
+        self.sizes[sid.value] = (width, height)
+        return sid.value
+
+    def close_session(self, sid: int):
+        N.check(N.lib().cloud_server_close_session(self._h, sid), "cloud_server_close_session")
+        self.sizes.pop(sid, None)
+
+    def submit(self, sid: int, cam: dict, steps: int) -> int:
+        t = ctypes.c_uint64()
+        c = N.camera(cam)
+        N.check(N.lib().cloud_server_submit(self._h, sid, ctypes.byref(c), steps, ctypes.byref(t)),
+                "cloud_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> dict:
+        info = N.RequestInfo()
+        N.check(N.lib().cloud_server_wait(self._h, ticket, timeout_ms, ctypes.byref(info)),
+                "cloud_server_wait")
+        return dict(session=info.session, steps=info.steps, batch_size=info.batch_size,
+                    queue_ms=info.queue_ms, latency_ms=info.latency_ms)
+
+    def output(self, sid: int):
+        """The session's latest resolved frame (history format) as a numpy array."""
+        w, h = self.sizes[sid]
+        dt = torch.float32 if self.history_fmt == "fp32" else torch.float16
+        host = torch.empty((h, w, 4), dtype=dt)
+        N.check(N.lib().cloud_server_copy_output(self._h, sid, ctypes.c_void_p(host.data_ptr()),
+                                                 host.numel() * host.element_size()),
+                "cloud_server_copy_output")
+        return host.numpy()
+
+    def pause(self, paused: bool = True):
+        N.check(N.lib().cloud_server_pause(self._h, 1 if paused else 0), "cloud_server_pause")
+
+    def stats(self) -> dict:
+        st = N.ServerCounters()
+        rc = N.lib().cloud_server_stats(self._h, ctypes.byref(st))
+        return dict(completed=st.completed, batches=st.batches, batched_views=st.batched_views,
+                    queued=st.queued, open_sessions=st.open_sessions,
+                    session_bytes=st.session_bytes, status=rc)
+
+    def close(self):
+        if self._h:
+            N.check(N.lib().cloud_server_destroy(self._h), "cloud_server_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,113 @@
+"""GPU: the continuous-batching render server (cloud_server_*).
+
+* a session's frames are the same alone and in a mix of concurrent sessions
+  (bitwise: each view is the same computation in any batch);
+* served frames match the FP64 oracle chain (render -> motion -> TAA);
+* sessions are admitted against a device-memory budget;
+* a paused server makes waits time out (host-side failure detection), and
+  the queued requests complete after it resumes."""
+import numpy as np
+import pytest
+
+from paper_1609_05344_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_05344_gb300 import _native, api as A
+    _native.build()
+    return A
+
+
+def _orbit(sid, f):
+    return I.orbit_camera(f, seed=100 + sid)
+
+
+def _run_alone(api, vol, w, h, frames, steps):
+    srv = api.Server(vol, I.params(), history_fmt="fp32", max_batch_views=8)
+    sid = srv.open_session(w, h)
+    outs = []
+    for f in range(frames):
+        srv.wait(srv.submit(sid, _orbit(0, f), steps))
+        outs.append(srv.output(sid))
+    srv.close()
+    return outs
+
+
+def test_same_alone_and_in_the_mix(api):
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    w, h, frames = 96, 64, 5
+    alone = _run_alone(api, vol, w, h, frames, 8)
+    srv = api.Server(vol, I.params(), history_fmt="fp32", max_batch_views=8, slots=2)
+    rng = np.random.default_rng(0)
+    sids = [srv.open_session(w, h)] + [srv.open_session(int(rng.integers(20, 200)),
+                                                        int(rng.integers(20, 120)))
+                                       for _ in range(7)]
+    mixed = []
+    for f in range(frames):
+        tickets = {}
+        order = list(rng.permutation(len(sids)))
+        for k in order:  # submit in random order; other sessions compete for the batch
+            tickets[k] = srv.submit(sids[k], _orbit(k, f), 16 if k % 2 else 8)
+        infos = {k: srv.wait(t) for k, t in tickets.items()}
+        mixed.append(srv.output(sids[0]))
+    st = srv.stats()
+    srv.close()
+    assert st["batches"] < st["completed"]  # requests were batched together
+    for a, m in zip(alone, mixed):
+        assert np.array_equal(a, m)
+
+
+def test_served_frames_match_oracle(api, oracle):
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    prm = I.params()
+    w, h = 80, 48
+    srv = api.Server(vol, prm, history_fmt="fp32")
+    sid = srv.open_session(w, h)
+    ohist = None
+    for f in range(4):
+        cam = _orbit(0, f)
+        srv.wait(srv.submit(sid, cam, 8))
+        ocur, _ = oracle.render(ovol, cam, prm, w, h, 8, 6, jitter_frame=f, nthreads=8)
+        omot = oracle.motion(desc, prm, _orbit(0, f - 1), cam, w, h) if f else np.zeros((h, w, 2))
+        ohist = oracle.taa(ohist, ocur, omot, blend=0.1)
+        assert np.abs(srv.output(sid).astype(np.float64) - ohist).max() <= 1e-4
+    srv.close()
+
+
+def test_admission_by_memory_budget(api):
+    from paper_1609_05344_gb300._native import CloudError, ERR_OUT_OF_MEMORY
+    vol = api.Volume(I.volume_desc("tiny"))
+    one = 640 * 360 * (16 + 8 + 2 * 8)  # current + motion + 2 FP16 histories
+    srv = api.Server(vol, I.params(), history_fmt="fp16", budget_bytes=3 * one)
+    sids = [srv.open_session(640, 360) for _ in range(3)]
+    with pytest.raises(CloudError) as e:
+        srv.open_session(640, 360)
+    assert e.value.status == ERR_OUT_OF_MEMORY
+    srv.close_session(sids[0])
+    sids[0] = srv.open_session(640, 360)  # freed memory admits a new session
+    assert srv.stats()["open_sessions"] == 3
+    srv.close()
+
+
+def test_pause_times_out_then_resumes(api):
+    from paper_1609_05344_gb300._native import CloudError, ERR_TIMEOUT
+    vol = api.Volume(I.volume_desc("tiny"))
+    srv = api.Server(vol, I.params())
+    sid = srv.open_session(64, 32)
+    srv.pause(True)
+    t = srv.submit(sid, _orbit(0, 0), 8)
+    with pytest.raises(CloudError) as e:
+        srv.wait(t, timeout_ms=100)
+    assert e.value.status == ERR_TIMEOUT
+    assert srv.stats()["queued"] == 1
+    srv.pause(False)
+    info = srv.wait(t, timeout_ms=10000)
+    assert info["latency_ms"] >= 100.0
+    srv.close()
