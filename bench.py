@@ -123,6 +123,19 @@ def dist_env():
         os.environ.get("LOCAL_RANK", 0))
 
 
+def make_reduce_max(world: int, device):
+    """Max over ranks of a per-rank number (NCCL on the GPU path, gloo on CPU)."""
+    def reduce_max(v: float) -> float:
+        if world == 1:
+            return v
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return reduce_max
+
+
 def aggregate(step_ms: float, samples: float, world: int, reduce_max=None):
     """Whole-job throughput: all ranks' samples over the slowest rank's time."""
     worst = reduce_max(step_ms) if reduce_max else step_ms
@@ -295,12 +308,7 @@ def run_gpu(args):
     taa_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(step_ms)
 
-    def reduce_max(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    reduce_max = make_reduce_max(world, "cuda")
 
     samples = W * H * S * (1 + LS)
     value, worst = aggregate(ms, samples, world, reduce_max)
