@@ -240,7 +240,6 @@ def run_gpu(args):
     vol = api.Volume(wl.volume)
     stream = torch.cuda.current_stream()
     cur = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
-    mot = torch.zeros((H, W, 2), dtype=torch.float32, device="cuda")
     hist = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -250,25 +249,22 @@ def run_gpu(args):
     state = {"latest": None, "n": 0}
 
     def frame(f, ev=None):
+        """One frame: raymarch (jitter frame f), then reprojection motion and TAA
+        resolve fused in one kernel.  Returns the number of launches."""
         if ev:
             ev[0].record(stream)
         api.render(vol, cam(f), prm, W, H, S, LS, jitter_frame=f, out=cur)
         if ev:
             ev[1].record(stream)
-        launches = 1
-        src = None
-        if state["latest"] is not None:
-            api.motion(vol, prm, cam(f - 1), cam(f), W, H, out=mot)
-            src = hist[state["latest"]]
-            launches += 1
-        if ev:
             ev[2].record(stream)
+        src = hist[state["latest"]] if state["latest"] is not None else None
         nxt = 1 if state["latest"] == 0 else 0
-        api.taa(src, cur, mot, blend=0.1, out=hist[nxt])
+        api.taa_reproject(vol, prm, cam(f - 1) if src is not None else None, cam(f), src, cur,
+                          blend=0.1, out=hist[nxt])
         if ev:
             ev[3].record(stream)
         state["latest"] = nxt
-        return launches + 1
+        return 2
 
     # clocks are sampled (every 200 ms) from the start of the warm-up through the
     # timed frames; warm-up continues, untimed, until the sampler is running
@@ -304,7 +300,6 @@ def run_gpu(args):
         dist.barrier()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     march_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    motion_ms = [e[1].elapsed_time(e[2]) for e in evs]
     taa_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(step_ms)
 
@@ -336,7 +331,8 @@ def run_gpu(args):
     march_avg = statistics.mean(march_ms)
     achieved = eff_lookups * bytes_per_lookup / (march_avg * 1e-3) / 1e9
     taa_avg = statistics.mean(taa_ms)
-    taa_gbs = W * H * 56 / (taa_avg * 1e-3) / 1e9
+    taa_bytes_px = 48  # current 16 + history 16 + resolved 16 (motion fused, never stored)
+    taa_gbs = W * H * taa_bytes_px / (taa_avg * 1e-3) / 1e9
 
     if rank != 0:
         if world > 1:
@@ -352,8 +348,8 @@ def run_gpu(args):
                    "volumes": "128^3 base + 32^3 detail + 512^2 weather",
                    "frames": "32-frame seeded orbit", "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
-        "ms_per_frame": worst, "march_ms": march_avg, "motion_ms": statistics.mean(motion_ms),
-        "taa_ms": taa_avg, "wall_ms_per_step_incl_flush": t_wall / args.steps * 1e3,
+        "ms_per_frame": worst, "march_ms": march_avg, "taa_reproject_ms": taa_avg,
+        "motion": "fused into the TAA resolve", "wall_ms_per_step_incl_flush": t_wall / args.steps * 1e3,
         "effective_lookups_per_frame": eff_lookups,
         "effective_gsamples_s": eff_lookups / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "l1tex", "achieved": achieved, "peak": l1_peak_gbs, "unit": "GB/s",
@@ -365,7 +361,8 @@ def run_gpu(args):
                      "sector_rate_peak": sector_peak_gbs,
                      "frac_of_sector_rate": achieved / sector_peak_gbs},
         "taa_roofline": {"bound": "hbm", "achieved": taa_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": taa_gbs / pk["hbm_gbs"], "bytes_per_pixel": 56,
+                         "frac": taa_gbs / pk["hbm_gbs"], "bytes_per_pixel": taa_bytes_px,
+                         "kernel": "taa_reproject_kernel",
                          "peak_source": pk["source"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                 "h2d_bytes_per_step": 216, "d2h_bytes_per_step": W * H * 16},

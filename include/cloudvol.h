@@ -286,18 +286,28 @@ int taa_resolve(const void *history, const float *current, const float *motion,
                 void *history_out, int width, int height, int history_fmt, float blend,
                 void *stream);
 
+/* cloud_motion followed by taa_resolve, fused into one kernel: the motion of
+ * each pixel (camera `prev` -> `cur`, exactly as cloud_motion computes it) is
+ * used in registers and never stored.  history == NULL is a first frame (prev
+ * may then be NULL).  Buffers as in taa_resolve. */
+int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
+                        const cloud_camera *cur, const void *history, const float *current,
+                        void *history_out, int width, int height, int history_fmt, float blend,
+                        void *stream);
+
 /* ---- sessions: one camera's stream of TAA frames ------------------------- */
 
-/* A session owns the device buffers of one view (current frame, motion,
- * two history buffers of history_fmt) and its frame index, which is the
- * jitter frame of Sec. 3.2.  The library allocates and owns the memory. */
+/* A session owns the device buffers of one view (current frame, two history
+ * buffers of history_fmt) and its frame index, which is the jitter frame of
+ * Sec. 3.2.  The library allocates and owns the memory. */
 int cloud_session_create(const cloud_volume *vol, int width, int height, int history_fmt,
                          cloud_session **out);
 int cloud_session_destroy(cloud_session *s);
 
-/* One frame: render with jitter_frame = the session's frame index, motion
- * from the previous frame's camera, TAA resolve into the other history
- * buffer, advance the index.  If host_out is not NULL the resolved frame
+/* One frame: render with jitter_frame = the session's frame index, then the
+ * fused reprojection (motion from the previous frame's camera) and TAA
+ * resolve into the other history buffer (cloud_taa_reproject), advance the
+ * index.  If host_out is not NULL the resolved frame
  * (width*height*4 values of the history format) is copied to it and the
  * call waits for the stream; otherwise it returns after enqueueing.
  * *dev_out (if not NULL) receives the device address of the resolved frame,

@@ -132,6 +132,28 @@ def taa(history, current: torch.Tensor, motion_px: torch.Tensor, blend: float = 
     return out
 
 
+def taa_reproject(vol: Volume, prm: dict, prev, cur: dict, history, current: torch.Tensor,
+                  blend: float = 0.1, out=None, history_fmt: str = "fp32", stream=None):
+    """Motion (prev -> cur) and TAA resolve fused (cloud_taa_reproject); history
+    None is a first frame."""
+    h, w = current.shape[:2]
+    dt = torch.float32 if history_fmt == "fp32" else torch.float16
+    if out is None:
+        out = torch.empty((h, w, 4), dtype=dt, device="cuda")
+    _require_cuda(current, "current", torch.float32)
+    _require_cuda(out, "out", dt)
+    if history is not None:
+        _require_cuda(history, "history", dt)
+    pc = N.camera(prev) if prev is not None else None
+    c, p = N.camera(cur), N.params(prm)
+    N.check(N.lib().cloud_taa_reproject(vol.handle, ctypes.byref(p),
+                                        ctypes.byref(pc) if pc is not None else None,
+                                        ctypes.byref(c), _ptr(history), _ptr(current), _ptr(out),
+                                        w, h, N.HISTORY[history_fmt], float(blend), _stream(stream)),
+            "cloud_taa_reproject")
+    return out
+
+
 class Session:
     """One camera's stream of jittered frames resolved by TAA (cloud_session_*)."""
 

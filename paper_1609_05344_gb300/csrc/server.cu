@@ -7,11 +7,11 @@
 // one request per session (a session's next frame needs the history its
 // previous frame produces) and at most max_batch_views requests, in arrival
 // order.  The batch's raymarch is one persistent launch over all its views,
-// followed by each request's motion and TAA resolve, all on the slot's
+// followed by each request's fused motion + TAA resolve, all on the slot's
 // stream; a host callback at the end of the stream work stamps the completion
 // time.  With two or more slots, a batch formed while another is on the GPU
-// overlaps with it.  Sessions keep their history, raw frame, motion and
-// jitter index on the device; opening one is admitted only while the free
+// overlaps with it.  Sessions keep their history, raw frame and jitter index
+// on the device; opening one is admitted only while the free
 // device memory stays above the configured reserve.  Every host wait is
 // bounded and reports CLOUD_ERR_TIMEOUT; nothing waits on the device without
 // a limit.
@@ -33,10 +33,10 @@ namespace cloudvol {
 int launch_batch(const cloud_volume *vol, const SceneParams &scene, const ViewParams *d_views,
                  int n_views, int total_tiles, int shape, unsigned int *d_work,
                  unsigned long long *counter, cudaStream_t s);
-int launch_motion(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
-                  const cloud_camera *cur, int width, int height, float *motion, cudaStream_t s);
-int launch_taa(const void *history, const float *current, const float *motion, void *history_out,
-               int width, int height, int fmt, float blend, cudaStream_t s);
+int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
+                         const cloud_camera *cur, const void *history, const float *current,
+                         void *history_out, int width, int height, int fmt, float blend,
+                         cudaStream_t s);
 }  // namespace cloudvol
 
 using namespace cloudvol;
@@ -52,7 +52,6 @@ double now_ms() {
 struct Session {
     int width = 0, height = 0;
     float *current = nullptr;  // raw jittered render
-    float *motion = nullptr;
     void *hist[2] = {nullptr, nullptr};
     int latest = 0;
     bool has_history = false;
@@ -169,17 +168,11 @@ int launch_slot(cloud_server *srv, int si, const std::vector<Request *> &batch) 
         const Request &r = *rp;
         Session &se = srv->sessions[r.session];
         const int nxt = 1 - se.latest;
-        int rc;
-        if (se.has_history) {
-            rc = launch_motion(srv->vol, &srv->prm, &se.prev_cam, &r.cam, se.width, se.height,
-                               se.motion, sl.stream);
-            if (!rc)
-                rc = launch_taa(se.hist[se.latest], se.current, se.motion, se.hist[nxt], se.width,
-                                se.height, srv->cfg.history_fmt, srv->cfg.blend, sl.stream);
-        } else {
-            rc = launch_taa(nullptr, se.current, se.motion, se.hist[nxt], se.width, se.height,
-                            srv->cfg.history_fmt, srv->cfg.blend, sl.stream);
-        }
+        // reprojection motion and TAA resolve fused (the motion is never stored)
+        const int rc = launch_taa_reproject(srv->vol, &srv->prm, se.has_history ? &se.prev_cam : nullptr,
+                                            &r.cam, se.has_history ? se.hist[se.latest] : nullptr,
+                                            se.current, se.hist[nxt], se.width, se.height,
+                                            srv->cfg.history_fmt, srv->cfg.blend, sl.stream);
         if (rc) return rc;
         // the session stays busy until this slot completes, so its state can advance now
         se.latest = nxt;
@@ -261,7 +254,6 @@ void worker_main(cloud_server *srv) {
 
 void free_session_buffers(Session &se) {
     if (se.current) cudaFree(se.current);
-    if (se.motion) cudaFree(se.motion);
     if (se.hist[0]) cudaFree(se.hist[0]);
     if (se.hist[1]) cudaFree(se.hist[1]);
     se = Session{};
@@ -351,7 +343,7 @@ extern "C" int cloud_server_open_session(cloud_server *srv, int width, int heigh
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_server_open_session: bad arguments");
     const size_t px = (size_t)width * height;
     const size_t hb = px * (srv->cfg.history_fmt == CLOUD_HISTORY_FP32 ? 16 : 8);
-    const size_t bytes = px * 16 + px * 8 + 2 * hb;
+    const size_t bytes = px * 16 + 2 * hb;  // raw frame + two histories
     std::lock_guard<std::mutex> lk(srv->mu);
     int id = -1;
     for (size_t i = 0; i < srv->sessions.size(); ++i)
@@ -375,7 +367,6 @@ extern "C" int cloud_server_open_session(cloud_server *srv, int width, int heigh
     se.height = height;
     se.bytes = bytes;
     int rc = check_cuda(cudaMalloc(&se.current, px * 16), "cudaMalloc current");
-    if (!rc) rc = check_cuda(cudaMalloc(&se.motion, px * 8), "cudaMalloc motion");
     if (!rc) rc = check_cuda(cudaMalloc(&se.hist[0], hb), "cudaMalloc history");
     if (!rc) rc = check_cuda(cudaMalloc(&se.hist[1], hb), "cudaMalloc history");
     if (rc) {

@@ -2,7 +2,7 @@
 // reduced-step render every frame, resolved against the reprojected history).
 //
 // The session owns its device buffers and the frame index that selects the
-// per-frame jitter; a frame is render -> motion -> TAA resolve -> swap.
+// per-frame jitter; a frame is render -> (motion + TAA resolve, fused) -> swap.
 #include <cstring>
 #include <new>
 
@@ -12,17 +12,16 @@ namespace cloudvol {
 int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
                   int width, int height, int steps, int light_steps, int jitter_frame,
                   int integration, float *out, unsigned long long *counter, cudaStream_t s);
-int launch_motion(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
-                  const cloud_camera *cur, int width, int height, float *motion, cudaStream_t s);
-int launch_taa(const void *history, const float *current, const float *motion, void *history_out,
-               int width, int height, int fmt, float blend, cudaStream_t s);
+int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
+                         const cloud_camera *cur, const void *history, const float *current,
+                         void *history_out, int width, int height, int fmt, float blend,
+                         cudaStream_t s);
 }  // namespace cloudvol
 
 struct cloud_session {
     const cloud_volume *vol;
     int width, height, fmt;
     float *current;  // device RGBA float, the raw jittered render
-    float *motion;   // device float2
     void *hist[2];   // device history ping-pong
     int latest;      // index of the latest resolved frame in hist
     bool has_history;
@@ -36,7 +35,6 @@ namespace {
 void free_session(cloud_session *s) {
     if (!s) return;
     if (s->current) cudaFree(s->current);
-    if (s->motion) cudaFree(s->motion);
     if (s->hist[0]) cudaFree(s->hist[0]);
     if (s->hist[1]) cudaFree(s->hist[1]);
     delete s;
@@ -60,7 +58,6 @@ extern "C" int cloud_session_create(const cloud_volume *vol, int width, int heig
     const size_t px = (size_t)width * height;
     const size_t hb = px * (history_fmt == CLOUD_HISTORY_FP32 ? 16 : 8);
     int rc = check_cuda(cudaMalloc(&s->current, px * 16), "cudaMalloc current");
-    if (!rc) rc = check_cuda(cudaMalloc(&s->motion, px * 8), "cudaMalloc motion");
     if (!rc) rc = check_cuda(cudaMalloc(&s->hist[0], hb), "cudaMalloc history");
     if (!rc) rc = check_cuda(cudaMalloc(&s->hist[1], hb), "cudaMalloc history");
     if (rc) {
@@ -96,15 +93,10 @@ extern "C" int cloud_session_frame(cloud_session *s, const cloud_camera *cam,
                            integration, s->current, nullptr, st);
     if (rc) return rc;
     const int next = 1 - s->latest;
-    if (s->has_history) {
-        rc = launch_motion(s->vol, prm, &s->prev_cam, cam, s->width, s->height, s->motion, st);
-        if (rc) return rc;
-        rc = launch_taa(s->hist[s->latest], s->current, s->motion, s->hist[next], s->width,
-                        s->height, s->fmt, blend, st);
-    } else {
-        rc = launch_taa(nullptr, s->current, s->motion, s->hist[next], s->width, s->height, s->fmt,
-                        blend, st);
-    }
+    // reprojection motion and TAA resolve fused (the motion is never stored)
+    rc = launch_taa_reproject(s->vol, prm, s->has_history ? &s->prev_cam : nullptr, cam,
+                              s->has_history ? s->hist[s->latest] : nullptr, s->current,
+                              s->hist[next], s->width, s->height, s->fmt, blend, st);
     if (rc) return rc;
     s->latest = next;
     s->has_history = true;

@@ -42,10 +42,7 @@ __device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, i
 // Motion of one pixel.  The motion is a small difference of nearly equal
 // pixel positions; it is computed directly as a difference of camera-space
 // slopes (no large terms cancel), so FP32 keeps it to ~1e-6 pixel.
-__global__ void __launch_bounds__(256) motion_kernel(const __grid_constant__ MotionParams p,
-                                                     float2 *__restrict__ motion) {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= p.width || y >= p.height) return;
+__device__ __forceinline__ float2 motion_at(const MotionParams &p, int x, int y) {
     const float a = fmaf((float)x, p.ax, p.a0), b = fmaf((float)y, p.by, p.b0);
     const float vlen = sqrtf(fmaf(a, a, fmaf(b, b, 1.0f)));
     const float vz = fmaf(a, p.rz, fmaf(b, p.uz, p.fz));
@@ -58,26 +55,24 @@ __global__ void __launch_bounds__(256) motion_kernel(const __grid_constant__ Mot
             lam = entry_lambda_exact(p, x, y, vlen);  // too close to call in FP32
         else if (l1 > l0 && l0 > 0.0f)
             lam = l0;
-    } else if (!p.cam_in_layer) {
-        lam = lmax;
     }
     const float g0 = fmaf(p.G[0][0], a, fmaf(p.G[0][1], b, p.G[0][2]));
     const float g1 = fmaf(p.G[1][0], a, fmaf(p.G[1][1], b, p.G[1][2]));
     const float g2 = fmaf(p.G[2][0], a, fmaf(p.G[2][1], b, p.G[2][2]));
     const float qz = fmaf(lam, 1.0f + g2, p.dlt[2]);
-    float2 m;
-    if (qz <= 0.0f) {
-        m = make_float2(1e9f, 1e9f);
-    } else {
-        // a kx qz - qx and qy - b ky qz, expanded so the O(lambda) terms cancel exactly
-        const float nx = fmaf(a * p.kx, p.dlt[2], -p.dlt[0]) +
-                         lam * fmaf(a, p.kx1, fmaf(a * p.kx, g2, -g0));
-        const float ny = fmaf(-b * p.ky, p.dlt[2], p.dlt[1]) +
-                         lam * fmaf(-b, p.ky1, fmaf(-b * p.ky, g2, g1));
-        const float iq = 1.0f / qz;
-        m = make_float2(p.sx * nx * iq, p.sy * ny * iq);
-    }
-    motion[(size_t)y * p.width + x] = m;
+    if (qz <= 0.0f) return make_float2(1e9f, 1e9f);
+    // a kx qz - qx and qy - b ky qz, expanded so the O(lambda) terms cancel exactly
+    const float nx = fmaf(a * p.kx, p.dlt[2], -p.dlt[0]) + lam * fmaf(a, p.kx1, fmaf(a * p.kx, g2, -g0));
+    const float ny = fmaf(-b * p.ky, p.dlt[2], p.dlt[1]) + lam * fmaf(-b, p.ky1, fmaf(-b * p.ky, g2, g1));
+    const float iq = 1.0f / qz;
+    return make_float2(p.sx * nx * iq, p.sy * ny * iq);
+}
+
+__global__ void __launch_bounds__(256) motion_kernel(const __grid_constant__ MotionParams p,
+                                                     float2 *__restrict__ motion) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= p.width || y >= p.height) return;
+    motion[(size_t)y * p.width + x] = motion_at(p, x, y);
 }
 
 __device__ __forceinline__ float4 load_hist(const float4 *h, size_t i) { return __ldg(h + i); }
@@ -159,6 +154,73 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
         }
     }
     store_hist(out, i, res);
+}
+
+// Reprojection and TAA resolve fused (Sec. 3.2): each pixel's motion is
+// computed in registers (motion_at, bitwise the motion kernel's value) instead
+// of being written and read back; the current frame's 3x3 neighbourhoods come
+// from a shared-memory tile with a clamped one-pixel halo; each thread
+// resolves two pixels (rows y and y + 8) so more loads are in flight.
+constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
+
+template <typename H>
+__global__ void __launch_bounds__(256) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
+                                                            const H *__restrict__ hist,
+                                                            const float4 *__restrict__ cur,
+                                                            H *__restrict__ out, float blend) {
+    __shared__ float4 tile[kTH + 2][kTW + 2];
+    const int W = mp.width, Hh = mp.height;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
+        const int ty = i / (kTW + 2), tx = i % (kTW + 2);
+        const int gx = min(max(x0 + tx - 1, 0), W - 1), gy = min(max(y0 + ty - 1, 0), Hh - 1);
+        tile[ty][tx] = __ldg(cur + (size_t)gy * W + gx);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int ly = threadIdx.y + 8 * r, y = y0 + ly;
+        if (x >= W || y >= Hh) continue;
+        const float4 c = tile[ly + 1][threadIdx.x + 1];
+        float4 res = c;
+        if (hist) {
+            const float2 m = motion_at(mp, x, y);
+            const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
+            const bool off = (m.x > xc) || (m.x < xc - (float)W) || (m.y > yc) || (m.y < yc - (float)Hh);
+            if (!off) {
+                const float nx = -m.x, ny = -m.y;
+                const float flx = floorf(nx), fly = floorf(ny);
+                const float fx = nx - flx, fy = ny - fly;
+                const int ix = x + (int)flx, iy = y + (int)fly;
+                const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
+                const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
+                const float4 h00 = load_hist(hist, (size_t)ya * W + xa);
+                const float4 h01 = load_hist(hist, (size_t)ya * W + xb);
+                const float4 h10 = load_hist(hist, (size_t)yb * W + xa);
+                const float4 h11 = load_hist(hist, (size_t)yb * W + xb);
+                float4 h = make_float4(bil(fx, fy, h00.x, h01.x, h10.x, h11.x),
+                                       bil(fx, fy, h00.y, h01.y, h10.y, h11.y),
+                                       bil(fx, fy, h00.z, h01.z, h10.z, h11.z),
+                                       bil(fx, fy, h00.w, h01.w, h10.w, h11.w));
+                float4 mn = c, mx = c;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        if (dx == 1 && dy == 1) continue;
+                        const float4 v = tile[ly + dy][threadIdx.x + dx];
+                        mn = fmin4(mn, v);
+                        mx = fmax4(mx, v);
+                    }
+                h = fmin4(fmax4(h, mn), mx);
+                res = make_float4(fmaf(blend, c.x - h.x, h.x), fmaf(blend, c.y - h.y, h.y),
+                                  fmaf(blend, c.z - h.z, h.z), fmaf(blend, c.w - h.w, h.w));
+            }
+        }
+        store_hist(out, (size_t)y * W + x, res);
+    }
 }
 
 int build_motion_params(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
@@ -260,6 +322,38 @@ int launch_taa(const void *history, const float *current, const float *motion, v
     return check_launch("taa_kernel");
 }
 
+int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
+                         const cloud_camera *cur, const void *history, const float *current,
+                         void *history_out, int width, int height, int fmt, float blend,
+                         cudaStream_t s) {
+    if (!vol || !prm || !cur || !current || !history_out || (history && !prev))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: null pointer");
+    if (fmt != CLOUD_HISTORY_FP32 && fmt != CLOUD_HISTORY_FP16)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: bad history format");
+    if (!(blend >= 0.0f && blend <= 1.0f))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: blend outside [0, 1]");
+    MotionParams p;
+    if (int rc = build_motion_params(vol, prm, history ? prev : cur, cur, width, height, &p)) return rc;
+    const size_t px = (size_t)width * height, eb = fmt == CLOUD_HISTORY_FP32 ? 16 : 8;
+    if (!aligned(current, 16) || !aligned(history_out, eb) || (history && !aligned(history, eb)))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: misaligned buffer");
+    if (history) {
+        const char *a = (const char *)history, *b = (const char *)history_out;
+        if (a < b + px * eb && b < a + px * eb)
+            return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: history and history_out overlap");
+    }
+    const dim3 grid((width + kTW - 1) / kTW, (height + kTH - 1) / kTH), block(32, 8);
+    if (fmt == CLOUD_HISTORY_FP32)
+        taa_reproject_kernel<float4><<<grid, block, 0, s>>>(p, (const float4 *)history,
+                                                            (const float4 *)current,
+                                                            (float4 *)history_out, blend);
+    else
+        taa_reproject_kernel<uint2><<<grid, block, 0, s>>>(p, (const uint2 *)history,
+                                                           (const float4 *)current,
+                                                           (uint2 *)history_out, blend);
+    return check_launch("taa_reproject_kernel");
+}
+
 }  // namespace cloudvol
 
 using namespace cloudvol;
@@ -277,4 +371,14 @@ extern "C" int taa_resolve(const void *history, const float *current, const floa
     clear_error();
     return launch_taa(history, current, motion, history_out, width, height, history_fmt, blend,
                       (cudaStream_t)stream);
+}
+
+extern "C" int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm,
+                                   const cloud_camera *prev, const cloud_camera *cur,
+                                   const void *history, const float *current, void *history_out,
+                                   int width, int height, int history_fmt, float blend,
+                                   void *stream) {
+    clear_error();
+    return launch_taa_reproject(vol, prm, prev, cur, history, current, history_out, width, height,
+                                history_fmt, blend, (cudaStream_t)stream);
 }

@@ -84,7 +84,7 @@ def test_served_frames_match_oracle(api, oracle):
 def test_admission_by_memory_budget(api):
     from paper_1609_05344_gb300._native import CloudError, ERR_OUT_OF_MEMORY
     vol = api.Volume(I.volume_desc("tiny"))
-    one = 640 * 360 * (16 + 8 + 2 * 8)  # current + motion + 2 FP16 histories
+    one = 640 * 360 * (16 + 2 * 8)  # current + 2 FP16 histories
     srv = api.Server(vol, I.params(), history_fmt="fp16", budget_bytes=3 * one)
     sids = [srv.open_session(640, 360) for _ in range(3)]
     with pytest.raises(CloudError) as e:

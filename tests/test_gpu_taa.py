@@ -99,3 +99,23 @@ def test_session_matches_oracle_chain(api, oracle, fmt, tol):
         print(f"session {fmt} frame {f}: max abs err {err:.3e}")
         assert err <= tol, (f, err)
     sess.close()
+
+
+@pytest.mark.parametrize("w,h", [(37, 23), (1920, 1080), (1, 1)])
+@pytest.mark.parametrize("fmt", ["fp32", "fp16"])
+def test_fused_reprojection_equals_separate(api, w, h, fmt):
+    import torch
+    rng = np.random.default_rng(w + h)
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    prm = I.params()
+    dt = np.float16 if fmt == "fp16" else np.float32
+    hist = _t(I.synthetic_frame(rng, h, w).astype(dt))
+    cur = _t(I.synthetic_frame(rng, h, w))
+    prev_cam, cur_cam = I.orbit_camera(4, 3), I.orbit_camera(5, 3)
+    mot = api.motion(vol, prm, prev_cam, cur_cam, w, h)
+    sep = api.taa(hist, cur, mot, blend=0.1, history_fmt=fmt).cpu().numpy()
+    fused = api.taa_reproject(vol, prm, prev_cam, cur_cam, hist, cur, blend=0.1,
+                              history_fmt=fmt).cpu().numpy()
+    assert np.array_equal(sep, fused)
+    first = api.taa_reproject(vol, prm, None, cur_cam, None, cur, history_fmt=fmt).cpu().numpy()
+    assert np.array_equal(first, api.taa(None, cur, mot, history_fmt=fmt).cpu().numpy())
