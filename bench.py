@@ -448,7 +448,7 @@ def run_batched(args):
                        "tile_shape": best, "shape_ms": times},
             "ms_persistent_no_graph": res["persistent"], "ms_one_launch_per_view": res["per_view"],
             "speedup_vs_per_view": res["per_view"] / ms,
-            "gpu_launches": 64 * 0 + 1, "clocks": dict(clk.summary(), window="all modes")}
+            "gpu_launches": args.steps, "clocks": dict(clk.summary(), window="all modes")}
     if rank == 0:
         print(json.dumps(line))
     batch.close()
