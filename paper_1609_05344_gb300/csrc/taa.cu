@@ -171,6 +171,34 @@ __global__ void __launch_bounds__(256) taa_reproject_kernel(const __grid_constan
     __shared__ float4 tile[kTH + 2][kTW + 2];
     const int W = mp.width, Hh = mp.height;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    const int x = x0 + threadIdx.x;
+    // 1. motion (registers only) and the history footprint of both pixels; the
+    //    history loads are issued before the current-frame tile so that the
+    //    two memory round trips overlap
+    bool use[2] = {false, false};
+    float fxs[2] = {0.f, 0.f}, fys[2] = {0.f, 0.f};
+    float4 h00[2], h01[2], h10[2], h11[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int y = y0 + threadIdx.y + 8 * r;
+        if (!hist || x >= W || y >= Hh) continue;
+        const float2 m = motion_at(mp, x, y);
+        const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
+        if ((m.x > xc) || (m.x < xc - (float)W) || (m.y > yc) || (m.y < yc - (float)Hh)) continue;
+        const float nx = -m.x, ny = -m.y;
+        const float flx = floorf(nx), fly = floorf(ny);
+        fxs[r] = nx - flx;
+        fys[r] = ny - fly;
+        const int ix = x + (int)flx, iy = y + (int)fly;
+        const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
+        const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
+        h00[r] = load_hist(hist, (size_t)ya * W + xa);
+        h01[r] = load_hist(hist, (size_t)ya * W + xb);
+        h10[r] = load_hist(hist, (size_t)yb * W + xa);
+        h11[r] = load_hist(hist, (size_t)yb * W + xb);
+        use[r] = true;
+    }
+    // 2. current-frame tile with a clamped one-pixel halo
     const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
         const int ty = i / (kTW + 2), tx = i % (kTW + 2);
@@ -178,46 +206,32 @@ __global__ void __launch_bounds__(256) taa_reproject_kernel(const __grid_constan
         tile[ty][tx] = __ldg(cur + (size_t)gy * W + gx);
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x;
+    // 3. clamp the filtered history to the 3x3 range and blend
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int ly = threadIdx.y + 8 * r, y = y0 + ly;
         if (x >= W || y >= Hh) continue;
         const float4 c = tile[ly + 1][threadIdx.x + 1];
         float4 res = c;
-        if (hist) {
-            const float2 m = motion_at(mp, x, y);
-            const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
-            const bool off = (m.x > xc) || (m.x < xc - (float)W) || (m.y > yc) || (m.y < yc - (float)Hh);
-            if (!off) {
-                const float nx = -m.x, ny = -m.y;
-                const float flx = floorf(nx), fly = floorf(ny);
-                const float fx = nx - flx, fy = ny - fly;
-                const int ix = x + (int)flx, iy = y + (int)fly;
-                const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
-                const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
-                const float4 h00 = load_hist(hist, (size_t)ya * W + xa);
-                const float4 h01 = load_hist(hist, (size_t)ya * W + xb);
-                const float4 h10 = load_hist(hist, (size_t)yb * W + xa);
-                const float4 h11 = load_hist(hist, (size_t)yb * W + xb);
-                float4 h = make_float4(bil(fx, fy, h00.x, h01.x, h10.x, h11.x),
-                                       bil(fx, fy, h00.y, h01.y, h10.y, h11.y),
-                                       bil(fx, fy, h00.z, h01.z, h10.z, h11.z),
-                                       bil(fx, fy, h00.w, h01.w, h10.w, h11.w));
-                float4 mn = c, mx = c;
+        if (use[r]) {
+            const float fx = fxs[r], fy = fys[r];
+            float4 h = make_float4(bil(fx, fy, h00[r].x, h01[r].x, h10[r].x, h11[r].x),
+                                   bil(fx, fy, h00[r].y, h01[r].y, h10[r].y, h11[r].y),
+                                   bil(fx, fy, h00[r].z, h01[r].z, h10[r].z, h11[r].z),
+                                   bil(fx, fy, h00[r].w, h01[r].w, h10[r].w, h11[r].w));
+            float4 mn = c, mx = c;
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
+            for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-                        if (dx == 1 && dy == 1) continue;
-                        const float4 v = tile[ly + dy][threadIdx.x + dx];
-                        mn = fmin4(mn, v);
-                        mx = fmax4(mx, v);
-                    }
-                h = fmin4(fmax4(h, mn), mx);
-                res = make_float4(fmaf(blend, c.x - h.x, h.x), fmaf(blend, c.y - h.y, h.y),
-                                  fmaf(blend, c.z - h.z, h.z), fmaf(blend, c.w - h.w, h.w));
-            }
+                for (int dx = 0; dx < 3; ++dx) {
+                    if (dx == 1 && dy == 1) continue;
+                    const float4 v = tile[ly + dy][threadIdx.x + dx];
+                    mn = fmin4(mn, v);
+                    mx = fmax4(mx, v);
+                }
+            h = fmin4(fmax4(h, mn), mx);
+            res = make_float4(fmaf(blend, c.x - h.x, h.x), fmaf(blend, c.y - h.y, h.y),
+                              fmaf(blend, c.z - h.z, h.z), fmaf(blend, c.w - h.w, h.w));
         }
         store_hist(out, (size_t)y * W + x, res);
     }
