@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
 constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
 
 template <typename H>
-__global__ void __launch_bounds__(256) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
+__global__ void __launch_bounds__(256, 4) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
                                                             const H *__restrict__ hist,
                                                             const float4 *__restrict__ cur,
                                                             H *__restrict__ out, float blend) {
