@@ -49,6 +49,9 @@ extern "C" {
 #define CLOUD_INTEGRATE_ANALYTIC 0 /* Sec. 3.1 analytic step integral            */
 #define CLOUD_INTEGRATE_BASIC 1    /* Sec. 3.1 basic S = T L                     */
 
+#define CLOUD_JITTER_PER_PIXEL 0 /* Sec. 3.2: random offset per pixel and frame   */
+#define CLOUD_JITTER_PER_FRAME 1 /* Sec. 4: one offset per frame for every ray    */
+
 #define CLOUD_HISTORY_FP32 0 /* TAA history: 4 x float per pixel (16 B)          */
 #define CLOUD_HISTORY_FP16 1 /* TAA history: 4 x IEEE half per pixel (8 B)       */
 
@@ -100,7 +103,9 @@ typedef struct {
  * any length, z > 0), sun colour x intensity, ambient radiance, the
  * Henyey-Greenstein asymmetry g in (-1, 1), absorption alpha per metre at
  * density 1, light-march step length, early-out optical depth (<= 0 turns the
- * early out off) and far clip of a view ray. */
+ * early out off), far clip of a view ray, and the jitter mode
+ * (CLOUD_JITTER_PER_PIXEL; CLOUD_JITTER_PER_FRAME shares one offset, that of
+ * pixel (0, 0), between all rays of a frame). */
 typedef struct {
     double sun_dir[3];
     double sun_radiance[3];
@@ -110,6 +115,7 @@ typedef struct {
     double light_step_m;
     double tau_max;
     double t_max_m;
+    int32_t jitter_mode;
 } cloud_params;
 
 /* One view of a multi-view launch: camera, image size, view steps, jitter

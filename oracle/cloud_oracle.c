@@ -299,7 +299,8 @@ static void unit_sun(const orc_params *prm, double s[3]) {
 
 /* ------------------------------------------------------------------------ */
 /* Raymarch of one pixel (Sec. 1 and Sec. 3.1).
- *   D = (t1 - t0)/N; sample i at t0 + (i + u) D, u the jitter (1/2 without).
+ *   D = (t1 - t0)/N; sample i at t0 + (i + u) D, u the jitter (1/2 without;
+ *   in per-frame mode the offset of pixel (0, 0) for every pixel).
  *   Light march (Sec. 1): Ls samples at p + (j + 1/2) dl s,
  *     tau_sun = alpha sum_j rho_j dl, only where rho_i > 0 (the step adds
  *     nothing otherwise).
@@ -323,7 +324,10 @@ void orc_render_pixel(const orc_volume *vol, const orc_camera *cam, const orc_pa
     if (!orc_slab_clip(&vol->d, prm, cam->pos, d, &t0, &t1)) return;
     unit_sun(prm, s);
     double D = (t1 - t0) / steps;
-    double u = jitter_frame < 0 ? 0.5 : orc_jitter(vol->d.seed, x, y, jitter_frame);
+    double u = 0.5;
+    if (jitter_frame >= 0)  /* Sec. 4: per-frame mode applies one offset to every ray */
+        u = prm->jitter_mode == ORC_JITTER_PER_FRAME ? orc_jitter(vol->d.seed, 0, 0, jitter_frame)
+                                                     : orc_jitter(vol->d.seed, x, y, jitter_frame);
     double phase = orc_hg(d[0] * s[0] + d[1] * s[1] + d[2] * s[2], prm->hg_g);
     double tau = 0.0, c[3] = {0.0, 0.0, 0.0};
     long long n_look = 0;

@@ -31,6 +31,10 @@ extern "C" {
 #define ORC_DENSITY_NOISE    0 /* fBm noise field (normal operation)            */
 #define ORC_DENSITY_CONSTANT 1 /* rho = constant everywhere (closed-form pins)  */
 
+/* Jitter of the start offset (Sec. 3.2; Sec. 4 compares the two). */
+#define ORC_JITTER_PER_PIXEL 0 /* a random offset per pixel and frame             */
+#define ORC_JITTER_PER_FRAME 1 /* one offset per frame, shared by every ray       */
+
 /* Per-step integration rules, Sec. 3.1. */
 #define ORC_INTEGRATE_ANALYTIC 0 /* S = T0 L int_0^D e^{-rho alpha x} dx       */
 #define ORC_INTEGRATE_BASIC    1 /* S = T L, transmittance updated first        */
@@ -77,6 +81,7 @@ typedef struct {
     double light_step;      /* light-march step length (m)                     */
     double tau_max;         /* early-out optical depth; <= 0 disables early out*/
     double t_max;           /* far clip of a view ray (m)                       */
+    int jitter_mode;        /* ORC_JITTER_PER_PIXEL or ORC_JITTER_PER_FRAME      */
 } orc_params;
 
 /* Counter-based hash (PCG output permutation over one LCG step). */

@@ -84,7 +84,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("sun_dir", _D3), ("sun_radiance", _D3), ("ambient", _D3),
                 ("hg_g", ctypes.c_double), ("absorption", ctypes.c_double),
                 ("light_step", ctypes.c_double), ("tau_max", ctypes.c_double),
-                ("t_max", ctypes.c_double)]
+                ("t_max", ctypes.c_double), ("jitter_mode", ctypes.c_int)]
 
 
 _P = ctypes.POINTER
@@ -175,7 +175,8 @@ def _cam(c: dict) -> _Cam:
 def _params(p: dict) -> _Params:
     return _Params(_vec3(p["sun_dir"]), _vec3(p["sun_radiance"]), _vec3(p["ambient"]),
                    float(p["hg_g"]), float(p["absorption"]), float(p["light_step"]),
-                   float(p["tau_max"]), float(p["t_max"]))
+                   float(p["tau_max"]), float(p["t_max"]),
+                   1 if p.get("jitter_mode", "pixel") == "frame" else 0)
 
 
 def _ptr(a: np.ndarray, ctype=ctypes.c_double):

@@ -29,6 +29,7 @@ PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "unorm16": 3}
 DENSITY = {"noise": 0, "constant": 1}
 INTEGRATION = {"analytic": 0, "basic": 1}
 HISTORY = {"fp32": 0, "fp16": 1}
+JITTER = {"pixel": 0, "frame": 1}
 MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM, MAX_VIEWS, STATIC_MAX_VIEWS = 32, 4096, 16384, 4096, 256
 
 
@@ -92,7 +93,8 @@ class Camera(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("sun_dir", _D3), ("sun_radiance", _D3), ("ambient", _D3), ("hg_g", ctypes.c_double),
                 ("absorption_per_m", ctypes.c_double), ("light_step_m", ctypes.c_double),
-                ("tau_max", ctypes.c_double), ("t_max_m", ctypes.c_double)]
+                ("tau_max", ctypes.c_double), ("t_max_m", ctypes.c_double),
+                ("jitter_mode", ctypes.c_int32)]
 
 
 class View(ctypes.Structure):
@@ -220,4 +222,4 @@ def camera(c: dict) -> Camera:
 def params(p: dict) -> Params:
     return Params(_D3(*p["sun_dir"]), _D3(*p["sun_radiance"]), _D3(*p["ambient"]), float(p["hg_g"]),
                   float(p["absorption"]), float(p["light_step"]), float(p["tau_max"]),
-                  float(p["t_max"]))
+                  float(p["t_max"]), JITTER[p.get("jitter_mode", "pixel")])

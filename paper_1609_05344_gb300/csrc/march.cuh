@@ -57,6 +57,7 @@ struct ViewParams {
     // miss_above (camera over it) cannot reach the layer within t_max
     float miss_below, miss_above;
     int cam_in_layer, width, height, steps, jitter_frame;
+    float u_frame;   // >= 0: the start offset of every ray (per-frame jitter); < 0: per pixel
     int tiles_x;     // tiles per image row
     int tile_begin;  // first work-queue index of this view (multi-view launches)
     int tile_count;
@@ -239,7 +240,9 @@ __device__ __forceinline__ unsigned long long march_tile(
             // --- a2: jittered start offset (Sec. 3.2) ---------------------------
             const df D = df_mul(df_add(lam1, df_neg(lam0)), {v.invn_h, v.invn_l});
             float u = 0.5f;
-            if (v.jitter_frame >= 0)
+            if (v.u_frame >= 0.0f)
+                u = v.u_frame;
+            else if (v.jitter_frame >= 0)
                 u = (float)(pcg_hash4((uint32_t)x, (uint32_t)y, (uint32_t)v.jitter_frame,
                                       p.jitter_key) >> 8) * (1.0f / 16777216.0f);
             const df lam_s = df_add(lam0, df_mulf(D, u));

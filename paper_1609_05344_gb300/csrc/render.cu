@@ -34,6 +34,8 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: light_steps outside [0, 32]");
     if (integration != CLOUD_INTEGRATE_ANALYTIC && integration != CLOUD_INTEGRATE_BASIC)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad integration mode");
+    if (prm->jitter_mode != CLOUD_JITTER_PER_PIXEL && prm->jitter_mode != CLOUD_JITTER_PER_FRAME)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad jitter mode");
     if (!(prm->t_max_m > 0.0 && prm->t_max_m <= 1e6) || !(prm->light_step_m >= 0.0) ||
         !(prm->absorption_per_m >= 0.0) || !(prm->hg_g > -1.0 && prm->hg_g < 1.0))
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: bad lighting constants");
@@ -139,6 +141,10 @@ int build_view(const cloud_volume *vol, const cloud_params *prm, const cloud_cam
     v->height = height;
     v->steps = steps;
     v->jitter_frame = jitter_frame < 0 ? -1 : jitter_frame;
+    v->u_frame = -1.0f;
+    if (jitter_frame >= 0 && prm->jitter_mode == CLOUD_JITTER_PER_FRAME)  // offset of pixel (0, 0)
+        v->u_frame = (float)(pcg_hash4(0u, 0u, (uint32_t)jitter_frame, d.seed ^ kJitterKey) >> 8) *
+                     (1.0f / 16777216.0f);
     int tw, th;
     tile_dims(shape, &tw, &th);
     v->tiles_x = (width + tw - 1) / tw;

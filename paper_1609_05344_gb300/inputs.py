@@ -33,7 +33,8 @@ SLAB_LO_M, SLAB_HI_M = 1500.0, 4000.0
 def params(**over) -> dict:
     """Lighting / march constants as a plain dictionary."""
     p = dict(sun_dir=SUN_DIR, sun_radiance=SUN_RADIANCE, ambient=AMBIENT, hg_g=HG_G,
-             absorption=ABSORPTION, light_step=LIGHT_STEP_M, tau_max=TAU_MAX, t_max=T_MAX_M)
+             absorption=ABSORPTION, light_step=LIGHT_STEP_M, tau_max=TAU_MAX, t_max=T_MAX_M,
+             jitter_mode="pixel")
     p.update(over)
     return p
 

@@ -68,6 +68,6 @@ def test_host_side_validation_without_gpu(lib):
 def test_struct_layouts_match_header():
     # field order and sizes of the descriptors mirror include/cloudvol.h
     assert ctypes.sizeof(N.Camera) == 13 * 8
-    assert ctypes.sizeof(N.Params) == 14 * 8
+    assert ctypes.sizeof(N.Params) == 15 * 8  # 14 doubles + jitter_mode (padded)
     assert N.VolumeDesc.seed.offset == 0 and N.VolumeDesc.detail_weight.offset == 16
     assert N.VolumeDesc.precision.offset == 88

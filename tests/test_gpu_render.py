@@ -231,3 +231,13 @@ def test_invalid_arguments_raise(api):
         api.render(vol, I.ground_camera(), I.params(sun_dir=(0.0, 1.0, -0.2)), 8, 8, 8, 6, out=out)
     with pytest.raises(CloudError):
         api.Volume(I.volume_desc("tiny", base_n=100))
+
+
+def test_per_frame_jitter_mode(api, oracle):
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    prm = I.params(jitter_mode="frame")
+    cam = I.orbit_camera(2, 3)
+    got = api.render(vol, cam, prm, 80, 45, 8, 6, jitter_frame=9).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, prm, 80, 45, 8, 6, jitter_frame=9, nthreads=8)
+    assert _max_err(got, ref) <= TOL_FP32

@@ -180,3 +180,25 @@ def test_convergence_in_step_count(oracle):
     assert np.abs(basic - ref).max() < 5e-3
     assert np.abs(basic - ref).max() < np.abs(
         oracle.render(vol, cam, prm, w, h, 256, 6, integration=oracle.BASIC, nthreads=4)[0] - ref).max()
+
+
+def test_per_frame_jitter_shares_one_offset(oracle):
+    # Sec. 4: "an identical random offset ... to every ray per frame": every pixel
+    # uses the offset of pixel (0, 0); alpha = 1 - exp(-alpha D sum rho(t0 + (i+u) D))
+    desc = I.volume_desc("tiny", seed=1)
+    prm = I.params(tau_max=0.0, jitter_mode="frame")
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    w, h, n = 12, 9, 8
+    img, _ = oracle.render(vol, cam, prm, w, h, n, 6, jitter_frame=5)
+    u = oracle.jitter(desc["seed"], 0, 0, 5)
+    for (x, y) in [(3, 2), (11, 8), (6, 4)]:
+        d = oracle.pixel_ray(cam, w, h, x, y)
+        hit, t0, t1 = oracle.slab_clip(desc, prm, cam["pos"], d)
+        if not hit:
+            continue
+        D = (t1 - t0) / n
+        rho = sum(vol.density(np.array(cam["pos"]) + (t0 + (i + u) * D) * d) for i in range(n))
+        assert img[y, x, 3] == pytest.approx(-math.expm1(-prm["absorption"] * D * rho), abs=1e-13)
+    pix, _ = oracle.render(vol, cam, I.params(tau_max=0.0), w, h, n, 6, jitter_frame=5)
+    assert not np.allclose(pix, img)  # per-pixel jitter differs
