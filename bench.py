@@ -559,6 +559,106 @@ def run_served(args):
     return 0
 
 
+# The paper's draw times (GTX 1080, Unity/RenderDoc, median of five; Sec. 4 table).
+PAPER_MS = {("full", 128, "none"): 297.7, ("half", 128, "none"): 128.0, ("half", 8, "none"): 2.3,
+            ("half", 8, "pixel"): 7.5, ("half", 8, "pixel+taa"): 7.5,
+            ("quarter", 8, "pixel+taa"): 2.4}
+
+
+def run_paper_table(args):
+    """The paper's Sec. 4 table re-measured on GB300 (1920x1080 display; half
+    and quarter read per axis), plus the per-frame-constant offset of Sec. 4,
+    and Fig. 1 / Fig. 2 as numbers: the error of each 8-step variant against
+    the 128-step image of the same static view (TAA accumulated 32 frames)."""
+    import numpy as np
+    import torch
+
+    from paper_1609_05344_gb300 import _native, api, inputs as I
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    _native.build()
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    cam = I.orbit_camera(0, 3)
+    res = {"full": (1920, 1080), "half": (960, 540), "quarter": (480, 270)}
+    flush = L2Flush()
+    stream = torch.cuda.current_stream()
+
+    def frame_fn(size, steps, mode):
+        w, h = res[size]
+        prm = I.params(jitter_mode="frame" if "frame" in mode else "pixel")
+        cur = torch.empty((h, w, 4), device="cuda")
+        hist = [torch.empty((h, w, 4), device="cuda") for _ in range(2)]
+        st = {"k": 0}
+
+        def run(f):
+            jf = f if mode != "none" else -1
+            api.render(vol, cam, prm, w, h, steps, 6, jitter_frame=jf, out=cur)
+            if "taa" in mode:
+                src = hist[st["k"] % 2] if f > 0 else None
+                api.taa_reproject(vol, prm, cam if src is not None else None, cam, src, cur,
+                                  out=hist[(st["k"] + 1) % 2])
+                st["k"] += 1
+        return run
+
+    rows = []
+    for size, steps, mode in [("full", 128, "none"), ("half", 128, "none"), ("half", 8, "none"),
+                              ("half", 8, "pixel"), ("half", 8, "pixel+taa"),
+                              ("quarter", 8, "pixel+taa"), ("half", 8, "frame"),
+                              ("half", 8, "frame+taa"), ("full", 8, "pixel+taa")]:
+        run = frame_fn(size, steps, mode)
+        for f in range(args.warmup):
+            run(f)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush(k)
+            evs[k][0].record(stream)
+            run(args.warmup + k)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+        rows.append({"resolution": size, "steps": steps, "jitter_taa": mode, "ms": ms,
+                     "paper_gtx1080_ms": PAPER_MS.get((size, steps, mode))})
+
+    # quality (half resolution, static view): error against the 128-step image
+    w, h = res["half"]
+    prm = I.params()
+    ref = api.render(vol, cam, prm, w, h, 128, 6).cpu().numpy().astype(np.float64)
+
+    def err(img):
+        d = img.astype(np.float64) - ref
+        return {"rmse_rgb": float(np.sqrt((d[..., :3] ** 2).mean())),
+                "mean_rgb": float(d[..., :3].mean()), "rmse_alpha": float(np.sqrt((d[..., 3] ** 2).mean()))}
+
+    q = {"8 steps": err(api.render(vol, cam, prm, w, h, 8, 6).cpu().numpy()),
+         "8 steps, basic S = T L": err(api.render(vol, cam, prm, w, h, 8, 6,
+                                                  integration="basic").cpu().numpy()),
+         "128 steps, basic S = T L": err(api.render(vol, cam, prm, w, h, 128, 6,
+                                                    integration="basic").cpu().numpy()),
+         "8 steps, jitter, 1 frame": err(api.render(vol, cam, prm, w, h, 8, 6,
+                                                    jitter_frame=0).cpu().numpy())}
+    for label, pm in (("8 steps, jitter, TAA 32 frames", prm),
+                      ("8 steps, per-frame jitter, TAA 32 frames", I.params(jitter_mode="frame"))):
+        cur = torch.empty((h, w, 4), device="cuda")
+        hist = None
+        for f in range(32):
+            api.render(vol, cam, pm, w, h, 8, 6, jitter_frame=f, out=cur)
+            hist = api.taa_reproject(vol, pm, cam if hist is not None else None, cam, hist, cur)
+        q[label] = err(hist.cpu().numpy())
+    half = next(r for r in rows if (r["resolution"], r["steps"], r["jitter_taa"]) ==
+                ("half", 8, "pixel+taa"))
+    line = {"metric": "ms/frame of the paper's Sec. 4 rows on GB300", "value": half["ms"],
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": half["ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper-table", "display": "1920x1080",
+                       "half": "960x540", "quarter": "480x270", "volumes": "full, FP32",
+                       "l2": "flushed between steps (256 MiB write + 256 MiB read, untimed)"},
+            "rows": rows, "quality_vs_128_steps_half_res": q}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -568,7 +668,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "unorm16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fast-1080p",
-                    choices=["fast-1080p", "batched-64", "served"])
+                    choices=["fast-1080p", "batched-64", "served", "paper-table"])
     args = ap.parse_args(argv)
     args.precision_set = any(a.startswith("--precision") for a in (argv or sys.argv[1:]))
     if args.warmup < 3:
@@ -579,6 +679,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "paper-table":
+        return run_paper_table(args)
     return run_gpu(args)
 
 
