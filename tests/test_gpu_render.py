@@ -241,3 +241,30 @@ def test_per_frame_jitter_mode(api, oracle):
     got = api.render(vol, cam, prm, 80, 45, 8, 6, jitter_frame=9).cpu().numpy()
     ref, _ = oracle.render(ovol, cam, prm, 80, 45, 8, 6, jitter_frame=9, nthreads=8)
     assert _max_err(got, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("ls", [1, 3, 32])
+def test_generic_light_step_counts(api, oracle, ls):
+    # light-step counts other than 6 use the generic (runtime-length) light loop
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    cam = I.orbit_camera(6, 3)
+    prm = I.params(light_step=40.0)
+    got = api.render(vol, cam, prm, 64, 36, 8, ls, jitter_frame=6).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, prm, 64, 36, 8, ls, jitter_frame=6, nthreads=8)
+    assert _max_err(got, ref) <= TOL_FP32
+
+
+def test_maximum_sizes(api, oracle):
+    desc = I.volume_desc("full", seed=3)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    cam = I.camera((0.0, 0.0, 500.0), 0.0, 25.0, 40.0)
+    # widest image (16384 x 3: a ragged row of tiles) and the most view steps
+    wide = api.render(vol, cam, I.params(), 16384, 3, 8, 6, jitter_frame=1).cpu().numpy()
+    xs = np.array([0, 1, 8191, 16383, 12345, 16382])
+    ys = np.array([0, 2, 1, 2, 0, 1])
+    ref, _ = oracle.render_pixels(ovol, cam, I.params(), 16384, 3, 8, 6, xs, ys, jitter_frame=1)
+    assert _max_err(wide[ys, xs], ref) <= TOL_FP32
+    deep = api.render(vol, cam, I.params(tau_max=0.0), 6, 4, 4096, 6).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, I.params(tau_max=0.0), 6, 4, 4096, 6, nthreads=8)
+    assert _max_err(deep, ref) <= TOL_FP32
