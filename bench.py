@@ -118,7 +118,7 @@ def march_traffic():
     import hashlib
     csrc = os.path.join(ROOT, "paper_1609_05344_gb300", "csrc")
     h = hashlib.sha1()
-    for f in ("render.cu", "common.cuh"):
+    for f in ("march.cuh", "render.cu", "common.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     prof = os.path.join(ROOT, "profiles", "march_kernel_fast-1080p.md")

@@ -18,6 +18,17 @@
 
 #include "common.cuh"
 
+// 1: fetch the detail record only after the base shows B > c (fewer L1 sectors,
+// one more dependent memory round trip); 0: fetch all records of a lookup at once.
+#ifndef CLOUDVOL_DETAIL_AFTER_BASE
+#define CLOUDVOL_DETAIL_AFTER_BASE 0
+#endif
+
+// CTAs per SM the march is compiled for (register budget 65536 / (128 x this)).
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS
+#define CLOUDVOL_MARCH_MIN_BLOCKS 6
+#endif
+
 namespace cloudvol {
 
 enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
@@ -154,9 +165,16 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
     if (g <= 0.0f) return 0.0f;
     float cb[8], cd[8], cw[4];
     load_rec8(base, rec3(p.log2_base, c[kBX], c[kBY], c[kBZ]), cb);
+#if !CLOUDVOL_DETAIL_AFTER_BASE
     if (detail) load_rec8(detail, rec3(p.log2_detail, c[kDX], c[kDY], c[kDZ]), cd);
+#endif
     if (weather) load_rec4(weather, rec2(p.log2_weather, c[kWX], c[kWY]), cw);
     const float b = trilerp(cb, p.log2_base, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
+#if CLOUDVOL_DETAIL_AFTER_BASE
+    // B <= c: the (non-negative) detail term cannot make the density positive
+    if (b + p.b_cut <= 0.0f) return 0.0f;
+    if (detail) load_rec8(detail, rec3(p.log2_detail, c[kDX], c[kDY], c[kDZ]), cd);
+#endif
     float r = b + p.k0;
     if (detail) {
         const float dt = trilerp(cd, p.log2_detail, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();
@@ -392,8 +410,3 @@ int build_view(const cloud_volume *vol, const cloud_params *prm, const cloud_cam
 int tuned_shape(int precision, int light_steps);
 
 }  // namespace cloudvol
-
-// CTAs per SM the march is compiled for (register budget 65536 / (128 x this)).
-#ifndef CLOUDVOL_MARCH_MIN_BLOCKS
-#define CLOUDVOL_MARCH_MIN_BLOCKS 6
-#endif
