@@ -322,6 +322,19 @@ int cloud_session_frame(cloud_session *s, const cloud_camera *cam, const cloud_p
                         int steps, int light_steps, int integration, float blend,
                         void *host_out, const void **dev_out, void *stream);
 
+/* As cloud_session_frame, but the copy of the resolved frame into host_out
+ * (pinned host memory recommended) runs on the session's own copy stream and
+ * the call returns at once, so the read-back of frame k overlaps the render of
+ * frame k+1; a later frame's resolve waits for the copy out of the history
+ * buffer it overwrites.  *frame_index receives this frame's index; host_out is
+ * complete after cloud_session_wait_frame(s, index). */
+int cloud_session_frame_async(cloud_session *s, const cloud_camera *cam, const cloud_params *prm,
+                              int steps, int light_steps, int integration, float blend,
+                              void *host_out, int *frame_index, void *stream);
+/* Waits at most timeout_ms (CLOUD_ERR_TIMEOUT) for the read-back of a frame
+ * issued by cloud_session_frame_async. */
+int cloud_session_wait_frame(cloud_session *s, int frame_index, int timeout_ms);
+
 /* Forgets the history: the next frame is a first frame (index kept). */
 int cloud_session_reset(cloud_session *s);
 

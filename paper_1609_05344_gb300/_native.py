@@ -146,6 +146,9 @@ SIGNATURES = [
     ("cloud_session_frame", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, ctypes.c_float, _vp,
                                  _P(_vp), _vp]),
     ("cloud_session_reset", _i, [_vp]),
+    ("cloud_session_frame_async", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, ctypes.c_float,
+                                       _vp, _ip, _vp]),
+    ("cloud_session_wait_frame", _i, [_vp, _i, _i]),
     ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
     ("cloud_autotune_render", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, _i, _i, _i, _vp, _i,
                                    _fp, _ip, _vp]),

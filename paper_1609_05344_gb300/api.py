@@ -178,6 +178,23 @@ class Session:
     def reset(self):
         N.check(N.lib().cloud_session_reset(self._h), "cloud_session_reset")
 
+    def frame_async(self, cam: dict, prm: dict, steps: int, light_steps: int, host_out,
+                    blend: float = 0.1, integration: str = "analytic", stream=None) -> int:
+        """Render + resolve one frame and start copying it into host_out on the
+        session's copy stream; returns the frame index to pass to wait_frame."""
+        c, p = N.camera(cam), N.params(prm)
+        idx = ctypes.c_int()
+        N.check(N.lib().cloud_session_frame_async(self._h, ctypes.byref(c), ctypes.byref(p), steps,
+                                                  light_steps, N.INTEGRATION[integration],
+                                                  float(blend), ctypes.c_void_p(host_out.data_ptr()),
+                                                  ctypes.byref(idx), _stream(stream)),
+                "cloud_session_frame_async")
+        return idx.value
+
+    def wait_frame(self, index: int, timeout_ms: int = 10000):
+        N.check(N.lib().cloud_session_wait_frame(self._h, index, timeout_ms),
+                "cloud_session_wait_frame")
+
     def frame(self, cam: dict, prm: dict, steps: int, light_steps: int, blend: float = 0.1,
               integration: str = "analytic", host_out=None, stream=None):
         """Render + motion + resolve one frame.  With host_out (a pinned CPU

@@ -3,8 +3,10 @@
 //
 // The session owns its device buffers and the frame index that selects the
 // per-frame jitter; a frame is render -> (motion + TAA resolve, fused) -> swap.
+#include <chrono>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "common.cuh"
 
@@ -27,6 +29,13 @@ struct cloud_session {
     bool has_history;
     int frame;
     cloud_camera prev_cam;
+    // asynchronous read-back: D2H copies of resolved frames run on their own
+    // stream; copied[i] marks the end of the last copy out of hist[i], so the
+    // resolve that next overwrites hist[i] waits for it
+    cudaStream_t copy_stream;
+    cudaEvent_t resolved[2], copied[2];
+    bool copy_pending[2];
+    int copy_frame[2];  // frame index whose copy was last issued from hist[i]
 };
 
 using namespace cloudvol;
@@ -34,6 +43,12 @@ using namespace cloudvol;
 namespace {
 void free_session(cloud_session *s) {
     if (!s) return;
+    if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+    for (int i = 0; i < 2; ++i) {
+        if (s->resolved[i]) cudaEventDestroy(s->resolved[i]);
+        if (s->copied[i]) cudaEventDestroy(s->copied[i]);
+    }
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->current) cudaFree(s->current);
     if (s->hist[0]) cudaFree(s->hist[0]);
     if (s->hist[1]) cudaFree(s->hist[1]);
@@ -60,6 +75,13 @@ extern "C" int cloud_session_create(const cloud_volume *vol, int width, int heig
     int rc = check_cuda(cudaMalloc(&s->current, px * 16), "cudaMalloc current");
     if (!rc) rc = check_cuda(cudaMalloc(&s->hist[0], hb), "cudaMalloc history");
     if (!rc) rc = check_cuda(cudaMalloc(&s->hist[1], hb), "cudaMalloc history");
+    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking),
+                             "cudaStreamCreate");
+    for (int i = 0; i < 2 && !rc; ++i) {
+        rc = check_cuda(cudaEventCreateWithFlags(&s->resolved[i], cudaEventDisableTiming), "cudaEventCreate");
+        if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming), "cudaEventCreate");
+        s->copy_frame[i] = -1;
+    }
     if (rc) {
         free_session(s);
         return rc;
@@ -82,17 +104,20 @@ extern "C" int cloud_session_reset(cloud_session *s) {
     return CLOUD_OK;
 }
 
-extern "C" int cloud_session_frame(cloud_session *s, const cloud_camera *cam,
-                                   const cloud_params *prm, int steps, int light_steps,
-                                   int integration, float blend, void *host_out,
-                                   const void **dev_out, void *stream) {
-    clear_error();
-    if (!s || !cam || !prm) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_frame: null pointer");
-    cudaStream_t st = (cudaStream_t)stream;
+namespace {
+// Render + fused resolve of one frame on `st`; returns the history index written.
+int session_render(cloud_session *s, const cloud_camera *cam, const cloud_params *prm, int steps,
+                   int light_steps, int integration, float blend, cudaStream_t st, int *written) {
     int rc = launch_render(s->vol, cam, prm, s->width, s->height, steps, light_steps, s->frame,
                            integration, s->current, nullptr, st);
     if (rc) return rc;
     const int next = 1 - s->latest;
+    // a read-back of hist[next] still in flight must finish before it is overwritten
+    if (s->copy_pending[next]) {
+        rc = check_cuda(cudaStreamWaitEvent(st, s->copied[next], 0), "cudaStreamWaitEvent");
+        if (rc) return rc;
+        s->copy_pending[next] = false;
+    }
     // reprojection motion and TAA resolve fused (the motion is never stored)
     rc = launch_taa_reproject(s->vol, prm, s->has_history ? &s->prev_cam : nullptr, cam,
                               s->has_history ? s->hist[s->latest] : nullptr, s->current,
@@ -102,13 +127,82 @@ extern "C" int cloud_session_frame(cloud_session *s, const cloud_camera *cam,
     s->has_history = true;
     s->prev_cam = *cam;
     s->frame += 1;
-    if (dev_out) *dev_out = s->hist[s->latest];
+    *written = next;
+    return CLOUD_OK;
+}
+
+size_t frame_bytes(const cloud_session *s) {
+    return (size_t)s->width * s->height * (s->fmt == CLOUD_HISTORY_FP32 ? 16 : 8);
+}
+}  // namespace
+
+extern "C" int cloud_session_frame(cloud_session *s, const cloud_camera *cam,
+                                   const cloud_params *prm, int steps, int light_steps,
+                                   int integration, float blend, void *host_out,
+                                   const void **dev_out, void *stream) {
+    clear_error();
+    if (!s || !cam || !prm) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_frame: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    int written = 0;
+    int rc = session_render(s, cam, prm, steps, light_steps, integration, blend, st, &written);
+    if (rc) return rc;
+    if (dev_out) *dev_out = s->hist[written];
     if (host_out) {
-        const size_t bytes = (size_t)s->width * s->height * (s->fmt == CLOUD_HISTORY_FP32 ? 16 : 8);
-        rc = check_cuda(cudaMemcpyAsync(host_out, s->hist[s->latest], bytes, cudaMemcpyDeviceToHost, st),
+        rc = check_cuda(cudaMemcpyAsync(host_out, s->hist[written], frame_bytes(s),
+                                        cudaMemcpyDeviceToHost, st),
                         "cudaMemcpyAsync resolved frame");
         if (rc) return rc;
         rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     }
     return rc;
+}
+
+extern "C" int cloud_session_frame_async(cloud_session *s, const cloud_camera *cam,
+                                         const cloud_params *prm, int steps, int light_steps,
+                                         int integration, float blend, void *host_out,
+                                         int *frame_index, void *stream) {
+    clear_error();
+    if (!s || !cam || !prm || !host_out)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_frame_async: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int index = s->frame;
+    int written = 0;
+    int rc = session_render(s, cam, prm, steps, light_steps, integration, blend, st, &written);
+    if (rc) return rc;
+    // the read-back runs on the copy stream, overlapping the next frame's render
+    rc = check_cuda(cudaEventRecord(s->resolved[written], st), "cudaEventRecord");
+    if (!rc) rc = check_cuda(cudaStreamWaitEvent(s->copy_stream, s->resolved[written], 0),
+                             "cudaStreamWaitEvent");
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(host_out, s->hist[written], frame_bytes(s),
+                                             cudaMemcpyDeviceToHost, s->copy_stream),
+                             "cudaMemcpyAsync resolved frame");
+    if (!rc) rc = check_cuda(cudaEventRecord(s->copied[written], s->copy_stream), "cudaEventRecord");
+    if (rc) return rc;
+    s->copy_pending[written] = true;
+    s->copy_frame[written] = index;
+    if (frame_index) *frame_index = index;
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_session_wait_frame(cloud_session *s, int frame_index, int timeout_ms) {
+    clear_error();
+    if (!s) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_wait_frame: null session");
+    // copies complete in issue order on the copy stream, so the earliest tracked
+    // copy at or after frame_index finishing implies that frame's copy finished
+    int slot = -1;
+    for (int i = 0; i < 2; ++i)
+        if (s->copy_frame[i] >= frame_index &&
+            (slot < 0 || s->copy_frame[i] < s->copy_frame[slot]))
+            slot = i;
+    if (frame_index < 0 || slot < 0)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_wait_frame: no such frame");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {  // bounded host-side polling of the copy's completion event
+        const cudaError_t q = cudaEventQuery(s->copied[slot]);
+        if (q == cudaSuccess) return CLOUD_OK;
+        if (q != cudaErrorNotReady) return check_cuda(q, "cudaEventQuery");
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+            return set_error(CLOUD_ERR_TIMEOUT, "cloud_session_wait_frame: read-back not finished");
+        std::this_thread::yield();
+    }
 }

@@ -119,3 +119,31 @@ def test_fused_reprojection_equals_separate(api, w, h, fmt):
     assert np.array_equal(sep, fused)
     first = api.taa_reproject(vol, prm, None, cur_cam, None, cur, history_fmt=fmt).cpu().numpy()
     assert np.array_equal(first, api.taa(None, cur, mot, history_fmt=fmt).cpu().numpy())
+
+
+def test_async_session_frames_match_sync(api):
+    import torch
+    desc = I.volume_desc("full", seed=3)
+    vol = api.Volume(desc)
+    prm = I.params()
+    w, h, frames = 200, 120, 7
+    ref = api.Session(vol, w, h)
+    host = torch.empty((h, w, 4), dtype=torch.float32, pin_memory=True)
+    want = []
+    for f in range(frames):
+        ref.frame(I.orbit_camera(f, 3), prm, 8, 6, host_out=host)
+        want.append(host.numpy().copy())
+    ref.close()
+    s = api.Session(vol, w, h)
+    bufs = [torch.empty((h, w, 4), dtype=torch.float32, pin_memory=True) for _ in range(3)]
+    idx = []
+    for f in range(frames):
+        idx.append(s.frame_async(I.orbit_camera(f, 3), prm, 8, 6, bufs[f % 3]))
+        if f >= 2:  # the oldest in-flight read-back, then its buffer is reused
+            s.wait_frame(idx[f - 2])
+            assert np.array_equal(bufs[(f - 2) % 3].numpy(), want[f - 2])
+    for f in (frames - 2, frames - 1):
+        s.wait_frame(idx[f])
+        assert np.array_equal(bufs[f % 3].numpy(), want[f])
+    s.wait_frame(idx[0])  # long finished: returns at once
+    s.close()
