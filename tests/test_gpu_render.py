@@ -181,7 +181,7 @@ def test_telescoping_no_sun_on_gpu(api):
 
 
 @pytest.mark.parametrize("case", ["inside-layer", "looking-down", "no-light-steps", "one-step",
-                                  "no-early-out", "horizontal"])
+                                  "no-early-out", "horizontal", "above-layer", "above-looking-up"])
 def test_edge_cases(api, oracle, case):
     desc = I.volume_desc("full", seed=5)
     vol, ovol = api.Volume(desc), oracle.Volume(desc)
@@ -200,12 +200,18 @@ def test_edge_cases(api, oracle, case):
         prm = I.params(tau_max=0.0)
     elif case == "horizontal":
         cam = I.camera((0.0, 0.0, 2000.0), 10.0, 0.0, 50.0)
+    elif case == "above-layer":  # enters from the top; rays near the horizon miss
+        cam = I.camera((300.0, -200.0, 6000.0), 70.0, -25.0, 70.0)
+    elif case == "above-looking-up":  # every ray misses (quick test from above)
+        cam = I.camera((300.0, -200.0, 6000.0), 70.0, 30.0, 40.0)
     w, h = 33, 17
     got = api.render(vol, cam, prm, w, h, steps, ls, jitter_frame=1).cpu().numpy()
     ref, _ = oracle.render(ovol, cam, prm, w, h, steps, ls, jitter_frame=1, nthreads=8)
     assert _max_err(got, ref) <= TOL_FP32
-    if case == "looking-down":
+    if case in ("looking-down", "above-looking-up"):
         assert np.all(got == 0.0)
+    if case == "above-layer":
+        assert ref[..., 3].max() > 0.5 and (ref[..., 3] == 0).any()
 
 
 def test_lookup_count_matches_oracle(api, oracle):

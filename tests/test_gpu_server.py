@@ -111,3 +111,23 @@ def test_pause_times_out_then_resumes(api):
     info = srv.wait(t, timeout_ms=10000)
     assert info["latency_ms"] >= 100.0
     srv.close()
+
+
+def test_failed_request_is_reported_not_hung(api):
+    # a request whose launch fails (camera with tan_half_fovy = 0) makes the
+    # server's error sticky: its wait and later submits report it, nothing hangs
+    from paper_1609_05344_gb300._native import CloudError, ERR_INVALID_ARG
+    vol = api.Volume(I.volume_desc("tiny"))
+    srv = api.Server(vol, I.params())
+    sid = srv.open_session(32, 16)
+    ok = srv.wait(srv.submit(sid, _orbit(0, 0), 8))
+    assert ok["latency_ms"] > 0
+    bad = dict(_orbit(0, 1), tan_half_fovy=0.0)
+    t = srv.submit(sid, bad, 8)
+    with pytest.raises(CloudError) as e:
+        srv.wait(t, timeout_ms=5000)
+    assert e.value.status == ERR_INVALID_ARG
+    assert srv.stats()["status"] == ERR_INVALID_ARG
+    with pytest.raises(CloudError):
+        srv.submit(sid, _orbit(0, 2), 8)
+    srv.close()
