@@ -519,3 +519,32 @@ void orc_taa(const double *history, const double *current, const double *motion,
             orc_taa_pixel(history, current, motion, width, height, x, y, blend, clamp,
                           out + 4 * ((size_t)y * width + x));
 }
+
+/* ------------------------------------------------------------------------ */
+/* Composite of the cloud buffer into the scene (Sec. 3.2).  [reading] The
+ * buffer is resampled to the display resolution bilinearly (texel centres at
+ * +1/2, clamp to edge) and, being premultiplied, laid over the background:
+ * out = C + (1 - alpha_C) bg, per channel including alpha. */
+void orc_composite(const double *cloud, int sw, int sh, const double *bg, int dw, int dh,
+                   double *out) {
+    for (int y = 0; y < dh; ++y)
+        for (int x = 0; x < dw; ++x) {
+            double u = (x + 0.5) * sw / dw - 0.5, v = (y + 0.5) * sh / dh - 0.5;
+            double fu = floor(u), fv = floor(v);
+            double fx = u - fu, fy = v - fv;
+            int xa = clampi((long long)fu, 0, sw - 1), xb = clampi((long long)fu + 1, 0, sw - 1);
+            int ya = clampi((long long)fv, 0, sh - 1), yb = clampi((long long)fv + 1, 0, sh - 1);
+            double c[4];
+            for (int k = 0; k < 4; ++k) {
+                double c00 = cloud[4 * ((size_t)ya * sw + xa) + k];
+                double c01 = cloud[4 * ((size_t)ya * sw + xb) + k];
+                double c10 = cloud[4 * ((size_t)yb * sw + xa) + k];
+                double c11 = cloud[4 * ((size_t)yb * sw + xb) + k];
+                c[k] = (1.0 - fy) * ((1.0 - fx) * c00 + fx * c01) + fy * ((1.0 - fx) * c10 + fx * c11);
+            }
+            for (int k = 0; k < 4; ++k) {
+                size_t i = 4 * ((size_t)y * dw + x) + k;
+                out[i] = c[k] + (1.0 - c[3]) * bg[i];
+            }
+        }
+}

@@ -137,6 +137,13 @@ void orc_taa_pixel(const double *history, const double *current, const double *m
 void orc_taa(const double *history, const double *current, const double *motion, int width,
              int height, double blend, int clamp, double *out);
 
+/* Composite (Sec. 3.2: the TAA-resolved low-resolution cloud buffer is
+ * composited into the scene).  cloud: sw x sh premultiplied RGBA; bg and out:
+ * dw x dh RGBA.  out = C + (1 - C.a) bg with C the bilinear sample of cloud at
+ * ((x + 1/2) sw/dw - 1/2, (y + 1/2) sh/dh - 1/2), clamp to edge. */
+void orc_composite(const double *cloud, int sw, int sh, const double *bg, int dw, int dh,
+                   double *out);
+
 #ifdef __cplusplus
 }
 #endif

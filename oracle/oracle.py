@@ -148,6 +148,9 @@ def _load():
         lib.orc_taa_pixel.argtypes = [_dp, _dp, _dp] + [ctypes.c_int] * 4 + [
             ctypes.c_double, ctypes.c_int, _dp]
         lib.orc_taa_pixel.restype = None
+        lib.orc_composite.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
+                                      ctypes.c_int, _dp]
+        lib.orc_composite.restype = None
         _lib = lib
         return lib
 
@@ -334,4 +337,15 @@ def taa(history, current, motion_px, blend: float = 0.1, clamp: bool = True):
         hist = np.ascontiguousarray(history, dtype=np.float64)
         hist_p = _ptr(hist)
     _load().orc_taa(hist_p, _ptr(cur), _ptr(mot), w, h, blend, 1 if clamp else 0, _ptr(out))
+    return out
+
+
+def composite(cloud, background):
+    """Bilinear upsample of the premultiplied cloud buffer to the background's
+    size, laid over it (Sec. 3.2 composite)."""
+    c = np.ascontiguousarray(cloud, dtype=np.float64)
+    b = np.ascontiguousarray(background, dtype=np.float64)
+    out = np.zeros_like(b)
+    _load().orc_composite(_ptr(c), c.shape[1], c.shape[0], _ptr(b), b.shape[1], b.shape[0],
+                          _ptr(out))
     return out

@@ -112,3 +112,18 @@ def test_taa_ema_closed_form(oracle):
     n = len(frames) - 1
     exp = (1 - b) ** n * frames[0] + sum(b * (1 - b) ** k * frames[n - k] for k in range(n))
     assert np.allclose(hist, exp, atol=1e-13, rtol=0)
+
+
+def test_composite_pins(oracle):
+    rng = np.random.default_rng(8)
+    cloud = I.synthetic_frame(rng, 10, 16).astype(np.float64)
+    bg = rng.uniform(0, 1, (20, 32, 4))
+    out = oracle.composite(cloud, bg)
+    # exact 2x upsample: output pixel (2i+1/2.., ) centres fall at +-1/4 texel; pixel (1,1)
+    # samples the cloud at (0.25, 0.25): weights 0.75/0.25 of texels 0 and 1
+    c = 0.5625 * cloud[0, 0] + 0.1875 * (cloud[0, 1] + cloud[1, 0]) + 0.0625 * cloud[1, 1]
+    assert np.allclose(out[1, 1], c + (1 - c[3]) * bg[1, 1], atol=1e-15)
+    # transparent cloud leaves the background; same size is a plain "over"
+    assert np.allclose(oracle.composite(np.zeros((4, 4, 4)), bg[:4, :4]), bg[:4, :4])
+    same = oracle.composite(cloud, bg[:10, :16])
+    assert np.allclose(same, cloud + (1 - cloud[..., 3:4]) * bg[:10, :16], atol=1e-15)
