@@ -579,6 +579,7 @@ PAPER_MS = {("full", 128, "none"): 297.7, ("half", 128, "none"): 128.0, ("half",
 def run_paper_table(args):
     """The paper's Sec. 4 table re-measured on GB300 (1920x1080 display; half
     and quarter read per axis), plus the per-frame-constant offset of Sec. 4,
+    the composite of the low-resolution buffer over a 1920x1080 background,
     and Fig. 1 / Fig. 2 as numbers: the error of each 8-step variant against
     the 128-step image of the same static view (TAA accumulated 32 frames)."""
     import numpy as np
@@ -599,6 +600,8 @@ def run_paper_table(args):
         prm = I.params(jitter_mode="frame" if "frame" in mode else "pixel")
         cur = torch.empty((h, w, 4), device="cuda")
         hist = [torch.empty((h, w, 4), device="cuda") for _ in range(2)]
+        bg = torch.rand((1080, 1920, 4), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+        disp = torch.empty_like(bg)
         st = {"k": 0}
 
         def run(f):
@@ -609,13 +612,17 @@ def run_paper_table(args):
                 api.taa_reproject(vol, prm, cam if src is not None else None, cam, src, cur,
                                   out=hist[(st["k"] + 1) % 2])
                 st["k"] += 1
+                if "composite" in mode:
+                    api.composite(hist[st["k"] % 2], bg, out=disp)
         return run
 
     rows = []
     for size, steps, mode in [("full", 128, "none"), ("half", 128, "none"), ("half", 8, "none"),
                               ("half", 8, "pixel"), ("half", 8, "pixel+taa"),
                               ("quarter", 8, "pixel+taa"), ("half", 8, "frame"),
-                              ("half", 8, "frame+taa"), ("full", 8, "pixel+taa")]:
+                              ("half", 8, "frame+taa"), ("full", 8, "pixel+taa"),
+                              ("half", 8, "pixel+taa+composite"),
+                              ("quarter", 8, "pixel+taa+composite")]:
         run = frame_fn(size, steps, mode)
         for f in range(args.warmup):
             run(f)

@@ -301,6 +301,15 @@ int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const 
                         void *history_out, int width, int height, int history_fmt, float blend,
                         void *stream);
 
+/* Composite (Sec. 3.2: the resolved cloud buffer is composited into the
+ * scene): the cloud buffer (cloud_width x cloud_height RGBA of cloud_fmt,
+ * CLOUD_HISTORY_*, premultiplied; e.g. a half- or quarter-resolution session
+ * output) is resampled bilinearly to width x height (texel centres, clamp to
+ * edge) and laid over `background` (device RGBA float, width x height):
+ * out = C + (1 - C.alpha) background.  out may equal background. */
+int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width, int cloud_height,
+                    const float *background, float *out, int width, int height, void *stream);
+
 /* ---- sessions: one camera's stream of TAA frames ------------------------- */
 
 /* A session owns the device buffers of one view (current frame, two history

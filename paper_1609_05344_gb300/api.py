@@ -154,6 +154,21 @@ def taa_reproject(vol: Volume, prm: dict, prev, cur: dict, history, current: tor
     return out
 
 
+def composite(cloud: torch.Tensor, background: torch.Tensor, out=None, stream=None):
+    """Upsample the premultiplied cloud buffer (float32 or float16 (h, w, 4)) to
+    the background's size and lay it over the background (cloud_composite)."""
+    _require_cuda(cloud, "cloud")
+    _require_cuda(background, "background", torch.float32)
+    fmt = "fp32" if cloud.dtype == torch.float32 else "fp16"
+    h, w = background.shape[:2]
+    if out is None:
+        out = torch.empty_like(background)
+    N.check(N.lib().cloud_composite(_ptr(cloud), N.HISTORY[fmt], cloud.shape[1], cloud.shape[0],
+                                    _ptr(background), _ptr(out), w, h, _stream(stream)),
+            "cloud_composite")
+    return out
+
+
 class Session:
     """One camera's stream of jittered frames resolved by TAA (cloud_session_*)."""
 

@@ -368,6 +368,62 @@ int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const
     return check_launch("taa_reproject_kernel");
 }
 
+// Composite (Sec. 3.2): the low-resolution cloud buffer, resampled
+// bilinearly to the display size, laid over the background (premultiplied
+// "over").  Streaming: the background is read and the result written once
+// (32 B per pixel); the small cloud buffer is served by L1/L2.
+// Source texel coordinate of output pixel x: u = (2x + 1) sw / (2 dw) - 1/2,
+// split into floor(u) and frac(u) with integer arithmetic so that the texel
+// choice is exact and frac is one correctly rounded division.
+__device__ __forceinline__ void src_coord(int x, int sw, int dw, int &i0, float &f) {
+    const int num = (2 * x + 1) * sw - dw, den = 2 * dw;  // < 2^31 for sizes <= 16384
+    const int q = num >= 0 ? num / den : -1;              // num >= -dw > -den
+    f = (float)(num - q * den) / (float)den;
+    i0 = q;
+}
+
+template <typename H>
+__global__ void __launch_bounds__(256) composite_kernel(const H *__restrict__ cloud, int sw, int sh,
+                                                        const float4 *__restrict__ bg, float4 *out,
+                                                        int dw, int dh) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= dw || y >= dh) return;
+    int u0, v0;
+    float fx, fy;
+    src_coord(x, sw, dw, u0, fx);
+    src_coord(y, sh, dh, v0, fy);
+    const int xa = max(u0, 0), xb = min(u0 + 1, sw - 1);
+    const int ya = max(v0, 0), yb = min(v0 + 1, sh - 1);
+    const float4 c00 = load_hist(cloud, (size_t)ya * sw + xa), c01 = load_hist(cloud, (size_t)ya * sw + xb);
+    const float4 c10 = load_hist(cloud, (size_t)yb * sw + xa), c11 = load_hist(cloud, (size_t)yb * sw + xb);
+    const float4 c = make_float4(bil(fx, fy, c00.x, c01.x, c10.x, c11.x), bil(fx, fy, c00.y, c01.y, c10.y, c11.y),
+                                 bil(fx, fy, c00.z, c01.z, c10.z, c11.z), bil(fx, fy, c00.w, c01.w, c10.w, c11.w));
+    const size_t i = (size_t)y * dw + x;
+    const float4 b = __ldg(bg + i);
+    const float t = 1.0f - c.w;
+    out[i] = make_float4(fmaf(t, b.x, c.x), fmaf(t, b.y, c.y), fmaf(t, b.z, c.z), fmaf(t, b.w, c.w));
+}
+
+int launch_composite(const void *cloud, int fmt, int sw, int sh, const float *bg, float *out, int dw,
+                     int dh, cudaStream_t s) {
+    if (!cloud || !bg || !out) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_composite: null pointer");
+    if (sw < 1 || sh < 1 || dw < 1 || dh < 1 || sw > CLOUD_MAX_DIM || sh > CLOUD_MAX_DIM ||
+        dw > CLOUD_MAX_DIM || dh > CLOUD_MAX_DIM)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_composite: sizes outside [1, 16384]");
+    if (fmt != CLOUD_HISTORY_FP32 && fmt != CLOUD_HISTORY_FP16)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_composite: bad cloud format");
+    if (!aligned(cloud, fmt == CLOUD_HISTORY_FP32 ? 16 : 8) || !aligned(bg, 16) || !aligned(out, 16))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_composite: misaligned buffer");
+    const dim3 grid((dw + 31) / 32, (dh + 7) / 8), block(32, 8);
+    if (fmt == CLOUD_HISTORY_FP32)
+        composite_kernel<float4><<<grid, block, 0, s>>>((const float4 *)cloud, sw, sh, (const float4 *)bg,
+                                                        (float4 *)out, dw, dh);
+    else
+        composite_kernel<uint2><<<grid, block, 0, s>>>((const uint2 *)cloud, sw, sh, (const float4 *)bg,
+                                                       (float4 *)out, dw, dh);
+    return check_launch("composite_kernel");
+}
+
 }  // namespace cloudvol
 
 using namespace cloudvol;
@@ -395,4 +451,12 @@ extern "C" int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *
     clear_error();
     return launch_taa_reproject(vol, prm, prev, cur, history, current, history_out, width, height,
                                 history_fmt, blend, (cudaStream_t)stream);
+}
+
+extern "C" int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width, int cloud_height,
+                               const float *background, float *out, int width, int height,
+                               void *stream) {
+    clear_error();
+    return launch_composite(cloud, cloud_fmt, cloud_width, cloud_height, background, out, width,
+                            height, (cudaStream_t)stream);
 }

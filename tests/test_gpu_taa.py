@@ -147,3 +147,17 @@ def test_async_session_frames_match_sync(api):
         assert np.array_equal(bufs[f % 3].numpy(), want[f])
     s.wait_frame(idx[0])  # long finished: returns at once
     s.close()
+
+
+@pytest.mark.parametrize("src,dst,fmt", [((960, 540), (1920, 1080), "fp32"),
+                                         ((480, 270), (1920, 1080), "fp16"),
+                                         ((37, 23), (100, 61), "fp32"), ((5, 3), (5, 3), "fp32")])
+def test_composite_parity(api, oracle, src, dst, fmt):
+    rng = np.random.default_rng(src[0])
+    cloud = I.synthetic_frame(rng, src[1], src[0])
+    if fmt == "fp16":
+        cloud = cloud.astype(np.float16)
+    bg = rng.uniform(0, 1, (dst[1], dst[0], 4)).astype(np.float32)
+    got = api.composite(_t(cloud), _t(bg)).cpu().numpy()
+    ref = oracle.composite(cloud.astype(np.float64), bg.astype(np.float64))
+    assert np.abs(got - ref).max() <= 1e-5
