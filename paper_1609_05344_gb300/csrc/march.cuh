@@ -24,12 +24,21 @@
 #define CLOUDVOL_DETAIL_AFTER_BASE 0
 #endif
 
-// CTAs per SM the march is compiled for (register budget 65536 / (128 x this)).
-#ifndef CLOUDVOL_MARCH_MIN_BLOCKS
-#define CLOUDVOL_MARCH_MIN_BLOCKS 6
+// CTAs per SM the march is compiled for (register budget 65536 / (128 x this)),
+// for FP32 records and for 16-bit records (which need fewer registers).
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32
+#define CLOUDVOL_MARCH_MIN_BLOCKS_F32 5
+#endif
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS_16
+#define CLOUDVOL_MARCH_MIN_BLOCKS_16 6
 #endif
 
 namespace cloudvol {
+
+template <typename T>
+struct MarchBlocks { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_16; };
+template <>
+struct MarchBlocks<float> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32; };
 
 enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
 

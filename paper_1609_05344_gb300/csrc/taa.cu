@@ -28,7 +28,7 @@ struct MotionParams {
 
 // Reprojection depth parameter lambda (t / |v|) of the layer entry point, or
 // of the far clip when the ray does not enter the layer ahead of the camera.
-__device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, int y, float vlen) {
+__device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, int y) {
     double v[3];
     for (int k = 0; k < 3; ++k) v[k] = fma((double)y, p.vy[k], fma((double)x, p.vx[k], p.v00[k]));
     const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -44,15 +44,18 @@ __device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, i
 // slopes (no large terms cancel), so FP32 keeps it to ~1e-6 pixel.
 __device__ __forceinline__ float2 motion_at(const MotionParams &p, int x, int y) {
     const float a = fmaf((float)x, p.ax, p.a0), b = fmaf((float)y, p.by, p.b0);
-    const float vlen = sqrtf(fmaf(a, a, fmaf(b, b, 1.0f)));
+    const float n2 = fmaf(a, a, fmaf(b, b, 1.0f));
     const float vz = fmaf(a, p.rz, fmaf(b, p.uz, p.fz));
-    const float lmax = p.tmax / vlen;
+    // divisions by hardware reciprocals (relative error ~1e-7, far below the
+    // 1e-5 margin of the near-tie test and the motion's own accuracy)
+    const float lmax = p.tmax * rsqrtf(n2);
     float lam = lmax;
-    if (fabsf(vz) >= 1e-8f * vlen) {
-        const float ll = p.zlo / vz, lh = p.zhi / vz;
+    if (fabsf(vz) >= 1e-8f * sqrtf(n2)) {
+        const float ivz = __fdividef(1.0f, vz);
+        const float ll = p.zlo * ivz, lh = p.zhi * ivz;
         const float l0 = fmaxf(fminf(ll, lh), 0.0f), l1 = fminf(fmaxf(ll, lh), lmax);
         if (fabsf(l1 - l0) <= 1e-5f * fmaxf(l1, l0))
-            lam = entry_lambda_exact(p, x, y, vlen);  // too close to call in FP32
+            lam = entry_lambda_exact(p, x, y);  // too close to call in FP32
         else if (l1 > l0 && l0 > 0.0f)
             lam = l0;
     }
@@ -64,7 +67,7 @@ __device__ __forceinline__ float2 motion_at(const MotionParams &p, int x, int y)
     // a kx qz - qx and qy - b ky qz, expanded so the O(lambda) terms cancel exactly
     const float nx = fmaf(a * p.kx, p.dlt[2], -p.dlt[0]) + lam * fmaf(a, p.kx1, fmaf(a * p.kx, g2, -g0));
     const float ny = fmaf(-b * p.ky, p.dlt[2], p.dlt[1]) + lam * fmaf(-b, p.ky1, fmaf(-b * p.ky, g2, g1));
-    const float iq = 1.0f / qz;
+    const float iq = __fdividef(1.0f, qz);
     return make_float2(p.sx * nx * iq, p.sy * ny * iq);
 }
 
@@ -159,22 +162,35 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
 // Reprojection and TAA resolve fused (Sec. 3.2): each pixel's motion is
 // computed in registers (motion_at, bitwise the motion kernel's value) instead
 // of being written and read back; the current frame's 3x3 neighbourhoods come
-// from a shared-memory tile with a clamped one-pixel halo; each thread
-// resolves two pixels (rows y and y + 8) so more loads are in flight.
+// from a shared-memory tile with a clamped one-pixel halo, copied with
+// cp.async while the motion is computed; each thread resolves two pixels
+// (rows y and y + 8) so more loads are in flight.
 constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem) : "memory");
+}
 
 template <typename H>
 __global__ void __launch_bounds__(256, 4) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
                                                             const H *__restrict__ hist,
                                                             const float4 *__restrict__ cur,
                                                             H *__restrict__ out, float blend) {
-    __shared__ float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(16) float4 tile[kTH + 2][kTW + 2];
     const int W = mp.width, Hh = mp.height;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const int x = x0 + threadIdx.x;
-    // 1. motion (registers only) and the history footprint of both pixels; the
-    //    history loads are issued before the current-frame tile so that the
-    //    two memory round trips overlap
+    // 1. current-frame tile with a clamped one-pixel halo, copied to shared
+    //    memory asynchronously while the motion is computed
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
+        const int ty = i / (kTW + 2), tx = i % (kTW + 2);
+        const int gx = min(max(x0 + tx - 1, 0), W - 1), gy = min(max(y0 + ty - 1, 0), Hh - 1);
+        cp_async16(&tile[ty][tx], cur + (size_t)gy * W + gx);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // 2. motion (registers only) and the history footprint of both pixels
     bool use[2] = {false, false};
     float fxs[2] = {0.f, 0.f}, fys[2] = {0.f, 0.f};
     float4 h00[2], h01[2], h10[2], h11[2];
@@ -198,13 +214,7 @@ __global__ void __launch_bounds__(256, 4) taa_reproject_kernel(const __grid_cons
         h11[r] = load_hist(hist, (size_t)yb * W + xb);
         use[r] = true;
     }
-    // 2. current-frame tile with a clamped one-pixel halo
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
-        const int ty = i / (kTW + 2), tx = i % (kTW + 2);
-        const int gx = min(max(x0 + tx - 1, 0), W - 1), gy = min(max(y0 + ty - 1, 0), Hh - 1);
-        tile[ty][tx] = __ldg(cur + (size_t)gy * W + gx);
-    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     // 3. clamp the filtered history to the 3x3 range and blend
 #pragma unroll
