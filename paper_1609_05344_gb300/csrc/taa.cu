@@ -100,8 +100,23 @@ __device__ __forceinline__ float4 fmin4(float4 a, float4 b) {
 __device__ __forceinline__ float4 fmax4(float4 a, float4 b) {
     return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
 }
-__device__ __forceinline__ float bil(float fx, float fy, float h00, float h01, float h10, float h11) {
-    return (1.0f - fy) * ((1.0f - fx) * h00 + fx * h01) + fy * ((1.0f - fx) * h10 + fx * h11);
+// a + t (b - a) on packed FP32x2 lanes (each lane rounds like the scalar form)
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t) {
+    return __ffma2_rn(make_float2(t, t), __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
+}
+// Bilinear filter of four RGBA texels: x on both rows, then y.
+__device__ __forceinline__ float4 bil4(float fx, float fy, float4 h00, float4 h01, float4 h10, float4 h11) {
+    const float2 xy = lerp2(lerp2(make_float2(h00.x, h00.y), make_float2(h01.x, h01.y), fx),
+                            lerp2(make_float2(h10.x, h10.y), make_float2(h11.x, h11.y), fx), fy);
+    const float2 zw = lerp2(lerp2(make_float2(h00.z, h00.w), make_float2(h01.z, h01.w), fx),
+                            lerp2(make_float2(h10.z, h10.w), make_float2(h11.z, h11.w), fx), fy);
+    return make_float4(xy.x, xy.y, zw.x, zw.y);
+}
+// TAA blend h + b (c - h) of the clamped history towards the current value
+__device__ __forceinline__ float4 blend4(float4 h, float4 c, float b) {
+    const float2 xy = lerp2(make_float2(h.x, h.y), make_float2(c.x, c.y), b);
+    const float2 zw = lerp2(make_float2(h.z, h.w), make_float2(c.z, c.w), b);
+    return make_float4(xy.x, xy.y, zw.x, zw.y);
 }
 
 // TAA resolve (Sec. 3.2): reprojected, bilinearly filtered history clamped
@@ -134,10 +149,7 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
             const float4 h01 = load_hist(hist, (size_t)ya * W + xb);
             const float4 h10 = load_hist(hist, (size_t)yb * W + xa);
             const float4 h11 = load_hist(hist, (size_t)yb * W + xb);
-            float4 h = make_float4(bil(fx, fy, h00.x, h01.x, h10.x, h11.x),
-                                   bil(fx, fy, h00.y, h01.y, h10.y, h11.y),
-                                   bil(fx, fy, h00.z, h01.z, h10.z, h11.z),
-                                   bil(fx, fy, h00.w, h01.w, h10.w, h11.w));
+            float4 h = bil4(fx, fy, h00, h01, h10, h11);
             float4 mn = c, mx = c;
 #pragma unroll
             for (int dy = -1; dy <= 1; ++dy) {
@@ -151,9 +163,7 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
                     mx = fmax4(mx, v);
                 }
             }
-            h = fmin4(fmax4(h, mn), mx);
-            res = make_float4(fmaf(blend, c.x - h.x, h.x), fmaf(blend, c.y - h.y, h.y),
-                              fmaf(blend, c.z - h.z, h.z), fmaf(blend, c.w - h.w, h.w));
+            res = blend4(fmin4(fmax4(h, mn), mx), c, blend);
         }
     }
     store_hist(out, i, res);
@@ -163,9 +173,12 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
 // computed in registers (motion_at, bitwise the motion kernel's value) instead
 // of being written and read back; the current frame's 3x3 neighbourhoods come
 // from a shared-memory tile with a clamped one-pixel halo, copied with
-// cp.async while the motion is computed; each thread resolves two pixels
-// (rows y and y + 8) so more loads are in flight.
+// cp.async while the motion is computed; each thread resolves two vertically
+// adjacent pixels, whose 3x3 windows share two rows.
 constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
+#ifndef CLOUDVOL_TAA_MIN_BLOCKS
+#define CLOUDVOL_TAA_MIN_BLOCKS 3  // CTAs per SM the fused kernel is compiled for (74 registers)
+#endif
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
@@ -173,30 +186,36 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 
 template <typename H>
-__global__ void __launch_bounds__(256, 4) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
+__global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
                                                             const H *__restrict__ hist,
                                                             const float4 *__restrict__ cur,
                                                             H *__restrict__ out, float blend) {
     __shared__ __align__(16) float4 tile[kTH + 2][kTW + 2];
     const int W = mp.width, Hh = mp.height;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    const int x = x0 + threadIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx;
     // 1. current-frame tile with a clamped one-pixel halo, copied to shared
-    //    memory asynchronously while the motion is computed
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
-        const int ty = i / (kTW + 2), tx = i % (kTW + 2);
-        const int gx = min(max(x0 + tx - 1, 0), W - 1), gy = min(max(y0 + ty - 1, 0), Hh - 1);
-        cp_async16(&tile[ty][tx], cur + (size_t)gy * W + gx);
+    //    memory asynchronously while the motion is computed: warp row ty copies
+    //    tile rows ty, ty + 8, ty + 16; lanes 0 and 1 also the two right columns
+    {
+        const int gx = min(max(x - 1, 0), W - 1), gx2 = min(x + 31, W - 1);
+#pragma unroll
+        for (int r = ty; r < kTH + 2; r += 8) {
+            const float4 *row = cur + (size_t)min(max(y0 + r - 1, 0), Hh - 1) * W;
+            cp_async16(&tile[r][tx], row + gx);
+            if (tx < 2) cp_async16(&tile[r][kTW + tx], row + gx2);
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // 2. motion (registers only) and the history footprint of both pixels
+    //    (rows 2 ty and 2 ty + 1 of the tile)
     bool use[2] = {false, false};
     float fxs[2] = {0.f, 0.f}, fys[2] = {0.f, 0.f};
     float4 h00[2], h01[2], h10[2], h11[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int y = y0 + threadIdx.y + 8 * r;
+        const int y = y0 + 2 * ty + r;
         if (!hist || x >= W || y >= Hh) continue;
         const float2 m = motion_at(mp, x, y);
         const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
@@ -216,32 +235,30 @@ __global__ void __launch_bounds__(256, 4) taa_reproject_kernel(const __grid_cons
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // 3. clamp the filtered history to the 3x3 range and blend
+    if (x >= W) return;
+    // 3. 3x3 ranges of both pixels from four tile rows (row-wise min/max, then
+    //    the two overlapping row triples share their middle pair), clamp the
+    //    filtered history, blend
+    float4 mn12, mx12;
+    {
+        const float4 a1 = tile[2 * ty + 1][tx], b1 = tile[2 * ty + 1][tx + 1], c1 = tile[2 * ty + 1][tx + 2];
+        const float4 a2 = tile[2 * ty + 2][tx], b2 = tile[2 * ty + 2][tx + 1], c2 = tile[2 * ty + 2][tx + 2];
+        mn12 = fmin4(fmin4(fmin4(a1, b1), c1), fmin4(fmin4(a2, b2), c2));
+        mx12 = fmax4(fmax4(fmax4(a1, b1), c1), fmax4(fmax4(a2, b2), c2));
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int ly = threadIdx.y + 8 * r, y = y0 + ly;
-        if (x >= W || y >= Hh) continue;
-        const float4 c = tile[ly + 1][threadIdx.x + 1];
+        const int y = y0 + 2 * ty + r;
+        if (y >= Hh) continue;
+        const float4 c = tile[2 * ty + r + 1][tx + 1];
         float4 res = c;
         if (use[r]) {
-            const float fx = fxs[r], fy = fys[r];
-            float4 h = make_float4(bil(fx, fy, h00[r].x, h01[r].x, h10[r].x, h11[r].x),
-                                   bil(fx, fy, h00[r].y, h01[r].y, h10[r].y, h11[r].y),
-                                   bil(fx, fy, h00[r].z, h01[r].z, h10[r].z, h11[r].z),
-                                   bil(fx, fy, h00[r].w, h01[r].w, h10[r].w, h11[r].w));
-            float4 mn = c, mx = c;
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    if (dx == 1 && dy == 1) continue;
-                    const float4 v = tile[ly + dy][threadIdx.x + dx];
-                    mn = fmin4(mn, v);
-                    mx = fmax4(mx, v);
-                }
-            h = fmin4(fmax4(h, mn), mx);
-            res = make_float4(fmaf(blend, c.x - h.x, h.x), fmaf(blend, c.y - h.y, h.y),
-                              fmaf(blend, c.z - h.z, h.z), fmaf(blend, c.w - h.w, h.w));
+            const int k = 2 * ty + 3 * r;  // the row of the pair's window not shared
+            const float4 a = tile[k][tx], b = tile[k][tx + 1], d = tile[k][tx + 2];
+            const float4 mn = fmin4(mn12, fmin4(fmin4(a, b), d));
+            const float4 mx = fmax4(mx12, fmax4(fmax4(a, b), d));
+            const float4 h = bil4(fxs[r], fys[r], h00[r], h01[r], h10[r], h11[r]);
+            res = blend4(fmin4(fmax4(h, mn), mx), c, blend);
         }
         store_hist(out, (size_t)y * W + x, res);
     }
@@ -406,8 +423,7 @@ __global__ void __launch_bounds__(256) composite_kernel(const H *__restrict__ cl
     const int ya = max(v0, 0), yb = min(v0 + 1, sh - 1);
     const float4 c00 = load_hist(cloud, (size_t)ya * sw + xa), c01 = load_hist(cloud, (size_t)ya * sw + xb);
     const float4 c10 = load_hist(cloud, (size_t)yb * sw + xa), c11 = load_hist(cloud, (size_t)yb * sw + xb);
-    const float4 c = make_float4(bil(fx, fy, c00.x, c01.x, c10.x, c11.x), bil(fx, fy, c00.y, c01.y, c10.y, c11.y),
-                                 bil(fx, fy, c00.z, c01.z, c10.z, c11.z), bil(fx, fy, c00.w, c01.w, c10.w, c11.w));
+    const float4 c = bil4(fx, fy, c00, c01, c10, c11);
     const size_t i = (size_t)y * dw + x;
     const float4 b = __ldg(bg + i);
     const float t = 1.0f - c.w;
