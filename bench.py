@@ -252,8 +252,9 @@ def run_gpu(args):
     _native.build()
 
     wl = I.workload("fast-1080p", precision=args.precision)
-    prm = I.params()
+    prm = I.params(jitter_mode="frame" if args.jitter == "frame" else "pixel")
     W, H, S, LS = wl.width, wl.height, wl.steps, wl.light_steps
+    jit = (lambda f: -1) if args.jitter == "none" else (lambda f: f)
     seed = wl.volume["seed"] + 1000 * rank  # each replica its own orbit start
     vol = api.Volume(wl.volume)
     stream = torch.cuda.current_stream()
@@ -271,7 +272,7 @@ def run_gpu(args):
         resolve fused in one kernel.  Returns the number of launches."""
         if ev:
             ev[0].record(stream)
-        api.render(vol, cam(f), prm, W, H, S, LS, jitter_frame=f, out=cur)
+        api.render(vol, cam(f), prm, W, H, S, LS, jitter_frame=jit(f), out=cur)
         if ev:
             ev[1].record(stream)
             ev[2].record(stream)
@@ -297,7 +298,7 @@ def run_gpu(args):
     # effective lookups per frame (untimed counting launches over the timed cameras)
     counted = []
     for k in range(min(args.steps, 8)):
-        _, ctr = api.render(vol, cam(fi + k), prm, W, H, S, LS, jitter_frame=fi + k, out=cur,
+        _, ctr = api.render(vol, cam(fi + k), prm, W, H, S, LS, jitter_frame=jit(fi + k), out=cur,
                             count=True)
         counted.append(int(ctr.item()))
     eff_lookups = statistics.mean(counted)
@@ -320,6 +321,34 @@ def run_gpu(args):
     march_ms = [e[0].elapsed_time(e[1]) for e in evs]
     taa_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(step_ms)
+
+    # the 32-frame orbit as one CUDA graph (render + fused resolve per frame), replayed
+    # back to back without L2 flushes: the steady state of a renderer whose tiles stay
+    # L2-resident between frames (reported beside, not as, the flushed number)
+    graph_ms = None
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(gs):
+            frame(fi + args.steps)  # first use of this stream, outside the capture
+        torch.cuda.current_stream().wait_stream(gs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            for k in range(wl.frames):
+                frame(fi + args.steps + 1 + k)
+        g.replay()
+        torch.cuda.synchronize()
+        ge = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ge[0].record()
+        for _ in range(3):
+            g.replay()
+        ge[1].record()
+        torch.cuda.synchronize()
+        graph_ms = ge[0].elapsed_time(ge[1]) / (3 * wl.frames)
+        del g
+    except RuntimeError as exc:  # capture is reported, never worked around
+        graph_ms = f"capture failed: {exc}"
 
     reduce_max = make_reduce_max(world, "cuda")
 
@@ -368,12 +397,16 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": worst, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "fast-1080p", "width": W, "height": H, "steps": S,
-                   "light_steps": LS, "jitter": True, "taa": True, "blend": 0.1,
+                   "light_steps": LS, "jitter": args.jitter, "taa": True, "blend": 0.1,
                    "volume_precision": args.precision,
                    "volumes": "128^3 base + 32^3 detail + 512^2 weather",
                    "frames": "32-frame seeded orbit", "l2": "flushed between steps (256 MiB write + 256 MiB read, untimed)",
                    "parallelism": f"replicas x{world}"},
         "ms_per_frame": worst, "march_ms": march_avg, "taa_reproject_ms": taa_avg,
+        "frame_ms_p10_p50_p90": [float(np.percentile(step_ms, q)) for q in (10, 50, 90)],
+        "graph_32_frames": {"ms_per_frame": graph_ms,
+                            "l2": "warm: 32 frames replayed back to back from one CUDA graph, "
+                                  "no flush between frames"},
         "motion": "fused into the TAA resolve", "wall_ms_per_step_incl_flush": t_wall / args.steps * 1e3,
         "effective_lookups_per_frame": eff_lookups,
         "effective_gsamples_s": eff_lookups / (ms * 1e-3) / 1e9,
@@ -685,6 +718,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "unorm16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jitter", default="pixel", choices=["pixel", "frame", "none"],
+                    help="fast-1080p start offsets: per pixel (Sec. 3.2), one per frame "
+                         "(Sec. 4), or none (midpoint samples)")
     ap.add_argument("--workload", default="fast-1080p",
                     choices=["fast-1080p", "batched-64", "served", "paper-table"])
     args = ap.parse_args(argv)
