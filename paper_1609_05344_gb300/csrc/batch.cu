@@ -22,7 +22,7 @@ namespace cloudvol {
 int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
                  unsigned long long *counter, int shape, cudaStream_t s);
 
-template <typename T, int LS, int SHAPE>
+template <typename T, int LS, int SHAPE, bool FX>
 __global__ void __launch_bounds__(128, MarchBlocks<T>::value)
     march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
                        int n_views, int total_tiles, unsigned int *__restrict__ work,
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(128, MarchBlocks<T>::value)
         for (int i = threadIdx.x; i < (int)(sizeof(ViewParams) / 4); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
         const int local = t - sv.tile_begin;
-        n_look += march_tile<T, LS, SHAPE>(p, sv, local % sv.tiles_x, local / sv.tiles_x,
+        n_look += march_tile<T, LS, SHAPE, FX>(p, sv, local % sv.tiles_x, local / sv.tiles_x,
                                            scratch[threadIdx.x >> 5], base, detail, weather);
         __syncthreads();  // s_tile / sv are rewritten by the next iteration
     }
@@ -62,25 +62,26 @@ __global__ void __launch_bounds__(128, MarchBlocks<T>::value)
 }
 
 template <typename T, int SHAPE>
-static const void *batch_kernel_ptr(int light_steps) {
-    return light_steps == 6 ? (const void *)march_batch_kernel<T, 6, SHAPE>
-                            : (const void *)march_batch_kernel<T, -1, SHAPE>;
+static const void *batch_kernel_ptr(int light_steps, bool fx) {
+    if (fx) return (const void *)march_batch_kernel<T, 6, SHAPE, true>;
+    return light_steps == 6 ? (const void *)march_batch_kernel<T, 6, SHAPE, false>
+                            : (const void *)march_batch_kernel<T, -1, SHAPE, false>;
 }
 template <typename T>
-static const void *batch_kernel_typed(int light_steps, int shape) {
+static const void *batch_kernel_typed(int light_steps, bool fx, int shape) {
     switch (shape) {
-        case 1: return batch_kernel_ptr<T, 1>(light_steps);
-        case 2: return batch_kernel_ptr<T, 2>(light_steps);
-        case 3: return batch_kernel_ptr<T, 3>(light_steps);
-        default: return batch_kernel_ptr<T, 0>(light_steps);
+        case 1: return batch_kernel_ptr<T, 1>(light_steps, fx);
+        case 2: return batch_kernel_ptr<T, 2>(light_steps, fx);
+        case 3: return batch_kernel_ptr<T, 3>(light_steps, fx);
+        default: return batch_kernel_ptr<T, 0>(light_steps, fx);
     }
 }
-static const void *batch_kernel(int precision, int light_steps, int shape) {
+static const void *batch_kernel(int precision, int light_steps, bool fx, int shape) {
     switch (precision) {
-        case CLOUD_PRECISION_FP32: return batch_kernel_typed<float>(light_steps, shape);
-        case CLOUD_PRECISION_FP16: return batch_kernel_typed<__half>(light_steps, shape);
-        case CLOUD_PRECISION_BF16: return batch_kernel_typed<__nv_bfloat16>(light_steps, shape);
-        default: return batch_kernel_typed<uint16_t>(light_steps, shape);
+        case CLOUD_PRECISION_FP32: return batch_kernel_typed<float>(light_steps, fx, shape);
+        case CLOUD_PRECISION_FP16: return batch_kernel_typed<__half>(light_steps, fx, shape);
+        case CLOUD_PRECISION_BF16: return batch_kernel_typed<__nv_bfloat16>(light_steps, fx, shape);
+        default: return batch_kernel_typed<uint16_t>(light_steps, fx, shape);
     }
 }
 
@@ -89,7 +90,7 @@ int launch_batch(const cloud_volume *vol, const SceneParams &scene, const ViewPa
                  int n_views, int total_tiles, int shape, unsigned int *d_work,
                  unsigned long long *counter, cudaStream_t s) {
     if (total_tiles == 0) return CLOUD_OK;
-    const void *fn = batch_kernel(vol->desc.precision, scene.light_steps, shape);
+    const void *fn = batch_kernel(vol->desc.precision, scene.light_steps, fixed_sizes(scene, vol), shape);
     int dev = 0, sms = 0, per_sm = 0;
     if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
     if (int rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),

@@ -40,6 +40,11 @@ struct MarchBlocks { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_16; 
 template <>
 struct MarchBlocks<float> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32; };
 
+// The standard tile sizes (128^3 base, 32^3 detail, 512^2 weather records) as
+// compile-time constants: with FX the record-index and weight shifts of every
+// lookup are immediates instead of per-launch values.
+constexpr int kStdLog2Base = 7, kStdLog2Detail = 5, kStdLog2Weather = 9;
+
 enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
 
 // Constants shared by every view of a launch: volume, lighting, light march.
@@ -162,35 +167,37 @@ __device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, ui
 // Samples outside the layer (g = 0) return without touching memory; otherwise
 // the three record loads are issued together so that one memory round trip
 // serves the lookup.
-template <typename T>
+template <bool FX, typename T>
 __device__ __forceinline__ float density(const SceneParams &p, const T *__restrict__ base,
                                          const T *__restrict__ detail,
                                          const T *__restrict__ weather, const uint32_t c[8],
                                          int32_t hq) {
-    if (p.constant_mode) return p.rho0;
+    const int lb = FX ? kStdLog2Base : p.log2_base, ld = FX ? kStdLog2Detail : p.log2_detail,
+              lw = FX ? kStdLog2Weather : p.log2_weather;
+    if (!FX && p.constant_mode) return p.rho0;
     const float ga = fminf(fmaxf((float)hq * p.h_lo_scale, 0.0f), 1.0f);
     const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
     const float g = ga * gb;
     if (g <= 0.0f) return 0.0f;
     float cb[8], cd[8], cw[4];
-    load_rec8(base, rec3(p.log2_base, c[kBX], c[kBY], c[kBZ]), cb);
+    load_rec8(base, rec3(lb, c[kBX], c[kBY], c[kBZ]), cb);
 #if !CLOUDVOL_DETAIL_AFTER_BASE
-    if (detail) load_rec8(detail, rec3(p.log2_detail, c[kDX], c[kDY], c[kDZ]), cd);
+    if (FX || detail) load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
 #endif
-    if (weather) load_rec4(weather, rec2(p.log2_weather, c[kWX], c[kWY]), cw);
-    const float b = trilerp(cb, p.log2_base, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
+    if (FX || weather) load_rec4(weather, rec2(lw, c[kWX], c[kWY]), cw);
+    const float b = trilerp(cb, lb, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
 #if CLOUDVOL_DETAIL_AFTER_BASE
     // B <= c: the (non-negative) detail term cannot make the density positive
     if (b + p.b_cut <= 0.0f) return 0.0f;
-    if (detail) load_rec8(detail, rec3(p.log2_detail, c[kDX], c[kDY], c[kDZ]), cd);
+    if (FX || detail) load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
 #endif
     float r = b + p.k0;
-    if (detail) {
-        const float dt = trilerp(cd, p.log2_detail, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();
+    if (FX || detail) {
+        const float dt = trilerp(cd, ld, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();
         r = fmaf(-p.detail_w, dt, r);
     }
     r = fmaxf(r * p.inv_1mc, 0.0f);
-    const float w = weather ? bilerp(cw, p.log2_weather, c[kWX], c[kWY]) - raw_bias<T>() + kCentre : 1.0f;
+    const float w = (FX || weather) ? bilerp(cw, lw, c[kWX], c[kWY]) - raw_bias<T>() + kCentre : 1.0f;
     return g * w * r;
 }
 
@@ -214,7 +221,7 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 //   C  each lane integrates its steps in order with the light sums from B.
 // The arithmetic of every sample is the same as a per-lane march.  Returns the
 // number of density lookups this lane performed.
-template <typename T, int LS, int SHAPE>
+template <typename T, int LS, int SHAPE, bool FX>
 __device__ __forceinline__ unsigned long long march_tile(
     const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch &ws,
     const T *__restrict__ base, const T *__restrict__ detail, const T *__restrict__ weather) {
@@ -325,7 +332,7 @@ __device__ __forceinline__ unsigned long long march_tile(
             for (int k = 0; k < kChunk; ++k) {
                 if (i0 + k >= v.steps) break;
                 // --- a3: density lookup ---------------------------------------
-                const float rho = density(p, base, detail, weather, c, hq);
+                const float rho = density<FX>(p, base, detail, weather, c, hq);
                 ws.rho[k][lane] = rho;
                 nA = k + 1;
                 if (rho > 0.0f) {
@@ -368,7 +375,7 @@ __device__ __forceinline__ unsigned long long march_tile(
                 uint32_t cj[kLatticeAxes];
 #pragma unroll
                 for (int a = 0; a < kLatticeAxes; ++a) cj[a] = cs[a] + p.loff[j][a];
-                rho_sum += density(p, base, detail, weather, cj, hs + p.lh[j]);
+                rho_sum += density<FX>(p, base, detail, weather, cj, hs + p.lh[j]);
             }
             ws.lsum[k][ow] = rho_sum;
         }
@@ -417,5 +424,8 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
 int build_view(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *cam, int width,
                int height, int steps, int jitter_frame, float *out, int shape, ViewParams *v);
 int tuned_shape(int precision, int light_steps);
+// True when a launch can use the FX march: the standard tile sizes, all three
+// tiles present, noise density and six light steps.
+bool fixed_sizes(const SceneParams &p, const cloud_volume *vol);
 
 }  // namespace cloudvol

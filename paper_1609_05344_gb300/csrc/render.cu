@@ -12,14 +12,14 @@
 
 namespace cloudvol {
 
-template <typename T, int LS, int SHAPE>
+template <typename T, int LS, int SHAPE, bool FX>
 __global__ void __launch_bounds__(128, MarchBlocks<T>::value)
     march_kernel(const __grid_constant__ SceneParams p, const __grid_constant__ ViewParams v,
                  const T *__restrict__ base, const T *__restrict__ detail,
                  const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
     __shared__ WarpScratch scratch[4];
     const unsigned long long n =
-        march_tile<T, LS, SHAPE>(p, v, blockIdx.x, blockIdx.y, scratch[threadIdx.x >> 5], base,
+        march_tile<T, LS, SHAPE, FX>(p, v, blockIdx.x, blockIdx.y, scratch[threadIdx.x >> 5], base,
                                  detail, weather);
     count_lookups(counter, n);
 }
@@ -171,6 +171,12 @@ void set_tuned_shape(int precision, int light_steps, int shape) {
     g_best_shape[precision & 3][light_steps == 6 ? 1 : 0] = shape;
 }
 
+bool fixed_sizes(const SceneParams &p, const cloud_volume *vol) {
+    return p.light_steps == 6 && !p.constant_mode && vol->detail && vol->weather &&
+           p.log2_base == kStdLog2Base && p.log2_detail == kStdLog2Detail &&
+           p.log2_weather == kStdLog2Weather;
+}
+
 template <typename T, int SHAPE>
 static void launch_shape(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
                          unsigned long long *counter, cudaStream_t s) {
@@ -178,10 +184,12 @@ static void launch_shape(const SceneParams &p, const ViewParams &v, const cloud_
     tile_dims(SHAPE, &tw, &th);
     const dim3 grid(v.tiles_x, (v.height + th - 1) / th);
     const T *b = (const T *)vol->base, *d = (const T *)vol->detail, *w = (const T *)vol->weather;
-    if (p.light_steps == 6)
-        march_kernel<T, 6, SHAPE><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
+    if (fixed_sizes(p, vol))
+        march_kernel<T, 6, SHAPE, true><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
+    else if (p.light_steps == 6)
+        march_kernel<T, 6, SHAPE, false><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
     else
-        march_kernel<T, -1, SHAPE><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
+        march_kernel<T, -1, SHAPE, false><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
 }
 
 template <typename T>
