@@ -23,7 +23,7 @@ int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *
                  unsigned long long *counter, int shape, cudaStream_t s);
 
 template <typename T, int LS, int SHAPE, bool FX>
-__global__ void __launch_bounds__(128, MarchBlocks<T>::value)
+__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
     march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
                        int n_views, int total_tiles, unsigned int *__restrict__ work,
                        const T *__restrict__ base, const T *__restrict__ detail,

@@ -35,10 +35,15 @@
 
 namespace cloudvol {
 
-template <typename T>
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX
+#define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX 5
+#endif
+template <typename T, bool FX>
 struct MarchBlocks { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_16; };
 template <>
-struct MarchBlocks<float> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32; };
+struct MarchBlocks<float, false> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32; };
+template <>
+struct MarchBlocks<float, true> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX; };
 
 // The standard tile sizes (128^3 base, 32^3 detail, 512^2 weather records) as
 // compile-time constants: with FX the record-index and weight shifts of every

@@ -13,7 +13,7 @@
 namespace cloudvol {
 
 template <typename T, int LS, int SHAPE, bool FX>
-__global__ void __launch_bounds__(128, MarchBlocks<T>::value)
+__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
     march_kernel(const __grid_constant__ SceneParams p, const __grid_constant__ ViewParams v,
                  const T *__restrict__ base, const T *__restrict__ detail,
                  const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
