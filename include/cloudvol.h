@@ -172,8 +172,8 @@ const char *cloud_last_error_message(void);
 /* ---- volumes ----------------------------------------------------------- */
 
 /* Creates the density volume described by *desc on the current device and
- * generates its noise tiles on `stream` (Sec. 1 "density is sampled"; field
- * as in cloud_volume_desc).  The library allocates and owns the device
+ * generates its noise tiles on `stream` (the density field Sec. 1
+ * samples; parameters as in cloud_volume_desc).  The library allocates and owns the device
  * memory; the handle may be shared read-only by any number of streams once
  * `stream` has passed the generation work.  *out is set only on success. */
 int cloud_volume_create(const cloud_volume_desc *desc, void *stream, cloud_volume **out);

@@ -5,9 +5,9 @@
  * beyond what the method itself states.
  *
  * Paper passages followed (Toft, Bowles, Zimmermann, arXiv 1609.05344):
- *   Sec. 1   rays fired into the volume, density sampled per step, colour and
- *            alpha accumulated, stop when alpha reaches 1 or the ray leaves
- *            the volume; running transmittance by Beer-Lambert; a second march
+ *   Sec. 1   one ray per pixel marched through the volume, density taken at
+ *            each step, colour and alpha accumulated, march ended once alpha
+ *            is one or the ray has left the volume; running transmittance by Beer-Lambert; a second march
  *            towards the sun per step; light colour x intensity x
  *            Henyey-Greenstein phase, plus an ambient term.
  *   Sec. 3.1 basic rule S = T L versus the analytic rule
@@ -59,8 +59,8 @@ void orc_hash4_batch(const uint32_t *keys, long n, uint32_t *out) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Value-noise fBm volumes.  [reading] The paper samples "the density" of a
- * cloud volume (Sec. 1) without defining it.  The field is four octaves of
+/* Value-noise fBm volumes.  [reading] Sec. 1 samples a cloud density at
+ * every step without defining the field.  The field is four octaves of
  * value noise: hashed uniform lattice values, plain trilinear interpolation,
  * octave o has M_o = (N/16) 2^o cells per tile and amplitude 2^-o, and the
  * sum is divided by the total amplitude.  Voxel k stores the noise at lattice
@@ -223,7 +223,7 @@ double orc_height_gradient(const orc_volume_desc *d, double z) {
     return a * b;
 }
 
-/* Density at a point (Sec. 1: "the density is sampled").  [reading]
+/* Density at a point (Sec. 1: sampled at every step).  [reading]
  * rho = g(z) * W(x,y) * max(0, (B - w_d Dt - c) / (1 - c)), with B the base
  * noise, Dt the detail noise (absent: 0), W the weather map (absent: 1) and c
  * the coverage threshold.  The constant mode returns rho0 everywhere. */
@@ -249,7 +249,7 @@ double orc_hg(double mu, double g) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Pinhole rays ("rays are fired into the volume", Sec. 1).  [reading]
+/* Pinhole rays, one per pixel (Sec. 1).  [reading]
  * d = normalize(F + a R + b U), a = (2(x+1/2)/W - 1) (W/H) tan(fovy/2),
  * b = (1 - 2(y+1/2)/H) tan(fovy/2). */
 void orc_pixel_ray(const orc_camera *cam, int width, int height, int x, int y, double d[3]) {
@@ -309,11 +309,11 @@ static void unit_sun(const orc_params *prm, double s[3]) {
  *     L = sigma L_in with sigma = alpha rho (single-scattering albedo 1), so
  *     the analytic step (Sec. 3.1, bound D) is
  *       C += e^{-tau} L_in (1 - e^{-sigma D}),  tau += sigma D
- *     and the basic step "updates the transmittance at a step, and then uses
- *     this value to update the colour":
+ *     and in the basic step the transmittance is first advanced over the
+ *     step and the advanced value then weights the step's light:
  *       tau += sigma D,  C += e^{-tau} sigma L_in D.
  *   Transmittance is e^{-tau} with tau the optical-depth sum (Beer-Lambert).
- *   [reading] Early out ("until the alpha reaches 1", Sec. 1): stop after the
+ *   [reading] Early out (Sec. 1: the march ends once alpha is one): stop after the
  *     step at which tau >= tau_max.  Alpha is reported as 1 - e^{-tau}. */
 void orc_render_pixel(const orc_volume *vol, const orc_camera *cam, const orc_params *prm,
                       int width, int height, int x, int y, int steps, int light_steps,

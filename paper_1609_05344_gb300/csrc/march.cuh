@@ -166,7 +166,7 @@ __device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, ui
     return fmaf(fy, xy.y - xy.x, xy.x);
 }
 
-// Density at a sample (Sec. 1 "the density is sampled"):
+// Density at a sample (Sec. 1):
 //   rho = g(h) W max(0, (B - w_d Dt - c)/(1 - c)),
 // tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0.
 // Samples outside the layer (g = 0) return without touching memory; otherwise

@@ -1,8 +1,8 @@
 // volume.cu -- cloud density volumes: creation, fBm generation, export, and
 // the device hash test hook.
 //
-// The paper samples "the density" of a cloud volume at every step (Sec. 1)
-// and does not define it.  The field here is value-noise fBm: 4 octaves,
+// Sec. 1 samples a cloud density at every step and does not define the
+// field.  The field here is value-noise fBm: 4 octaves,
 // octave o with (N/16) 2^o lattice cells per tile and amplitude 2^-o, summed
 // and divided by the total amplitude; lattice values are hash(ix, iy, iz,
 // seed ^ o*0x9E37 ^ salt) >> 8 scaled to [0,1); plain trilinear

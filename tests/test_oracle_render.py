@@ -183,7 +183,7 @@ def test_convergence_in_step_count(oracle):
 
 
 def test_per_frame_jitter_shares_one_offset(oracle):
-    # Sec. 4: "an identical random offset ... to every ray per frame": every pixel
+    # Sec. 4: one random offset shared by all rays of a frame; every pixel
     # uses the offset of pixel (0, 0); alpha = 1 - exp(-alpha D sum rho(t0 + (i+u) D))
     desc = I.volume_desc("tiny", seed=1)
     prm = I.params(tau_max=0.0, jitter_mode="frame")
