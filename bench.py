@@ -114,24 +114,36 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def march_traffic():
-    """DRAM bytes per march launch from the committed ncu summary, or None when
-    the kernel source has changed since those counters were taken."""
+def march_code_sha1():
+    """SHA-1 (12 hex digits) of the march sources with comments and blank lines
+    removed: it changes when the code does, not when a comment does."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_1609_05344_gb300", "csrc")
     h = hashlib.sha1()
     for f in ("march.cuh", "render.cu", "common.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            line = line.split("//")[0].rstrip()
+            if line:
+                h.update(line.encode() + b"\n")
+    return h.hexdigest()[:12]
+
+
+def march_traffic():
+    """DRAM bytes per march launch from the committed ncu summary, or None when
+    the kernel code has changed since those counters were taken."""
+    h = march_code_sha1()
     prof = os.path.join(ROOT, "profiles", "march_kernel_fast-1080p.md")
     if not os.path.exists(prof):
         return None
     vals = {}
     for line in open(prof):
-        if ":" in line and line.split(":")[0] in ("source_sha1", "traffic_bytes_per_launch"):
+        if ":" in line and line.split(":")[0] in ("code_sha1", "traffic_bytes_per_launch"):
             k, v = line.split(":", 1)
             vals[k] = v.strip()
-    if vals.get("source_sha1") != h.hexdigest()[:12]:
+    if vals.get("code_sha1") != h:
         return None
     return int(vals["traffic_bytes_per_launch"])
 
