@@ -41,34 +41,70 @@ __device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, i
 
 // Motion of one pixel.  The motion is a small difference of nearly equal
 // pixel positions; it is computed directly as a difference of camera-space
-// slopes (no large terms cancel), so FP32 keeps it to ~1e-6 pixel.
-__device__ __forceinline__ float2 motion_at(const MotionParams &p, int x, int y) {
-    const float a = fmaf((float)x, p.ax, p.a0), b = fmaf((float)y, p.by, p.b0);
-    const float n2 = fmaf(a, a, fmaf(b, b, 1.0f));
-    const float vz = fmaf(a, p.rz, fmaf(b, p.uz, p.fz));
+// slopes (no large terms cancel), so FP32 keeps it to ~1e-6 pixel.  Split in
+// three parts so that a thread can share the column terms between pixels and
+// interleave the arithmetic of several pixels: the column terms, the depth
+// parameter of the layer entry (FP32, with a flag for the near ties that the
+// FP64 restatement decides), and the projection into the previous camera.
+struct MotionCol {
+    float a, n2x, vzx, gx0, gx1, gx2, akx, nx0;
+};
+__device__ __forceinline__ MotionCol motion_col(const MotionParams &p, int x) {
+    MotionCol c;
+    c.a = fmaf((float)x, p.ax, p.a0);
+    c.n2x = fmaf(c.a, c.a, 1.0f);
+    c.vzx = fmaf(c.a, p.rz, p.fz);
+    c.gx0 = fmaf(p.G[0][0], c.a, p.G[0][2]);
+    c.gx1 = fmaf(p.G[1][0], c.a, p.G[1][2]);
+    c.gx2 = fmaf(p.G[2][0], c.a, p.G[2][2]);
+    c.akx = c.a * p.kx;
+    c.nx0 = fmaf(c.akx, p.dlt[2], -p.dlt[0]);
+    return c;
+}
+// Depth parameter lambda (t / |v|) of the layer entry, or of the far clip;
+// *exact is set when FP32 cannot call the entry (the caller then takes
+// entry_lambda_exact).  b is the row slope.
+__device__ __forceinline__ float motion_lambda(const MotionParams &p, const MotionCol &c, float b,
+                                               bool *exact) {
+    const float n2 = fmaf(b, b, c.n2x);
+    const float vz = fmaf(b, p.uz, c.vzx);
     // divisions by hardware reciprocals (relative error ~1e-7, far below the
     // 1e-5 margin of the near-tie test and the motion's own accuracy)
     const float lmax = p.tmax * rsqrtf(n2);
     float lam = lmax;
-    if (fabsf(vz) >= 1e-8f * sqrtf(n2)) {
+    *exact = false;
+    if (vz * vz >= 1e-16f * n2) {  // |d_z| >= 1e-8
         const float ivz = __fdividef(1.0f, vz);
         const float ll = p.zlo * ivz, lh = p.zhi * ivz;
         const float l0 = fmaxf(fminf(ll, lh), 0.0f), l1 = fminf(fmaxf(ll, lh), lmax);
         if (fabsf(l1 - l0) <= 1e-5f * fmaxf(l1, l0))
-            lam = entry_lambda_exact(p, x, y);  // too close to call in FP32
+            *exact = true;  // too close to call in FP32
         else if (l1 > l0 && l0 > 0.0f)
             lam = l0;
     }
-    const float g0 = fmaf(p.G[0][0], a, fmaf(p.G[0][1], b, p.G[0][2]));
-    const float g1 = fmaf(p.G[1][0], a, fmaf(p.G[1][1], b, p.G[1][2]));
-    const float g2 = fmaf(p.G[2][0], a, fmaf(p.G[2][1], b, p.G[2][2]));
+    return lam;
+}
+__device__ __forceinline__ float2 motion_project(const MotionParams &p, const MotionCol &c, float b,
+                                                 float lam) {
+    const float g0 = fmaf(p.G[0][1], b, c.gx0);
+    const float g1 = fmaf(p.G[1][1], b, c.gx1);
+    const float g2 = fmaf(p.G[2][1], b, c.gx2);
     const float qz = fmaf(lam, 1.0f + g2, p.dlt[2]);
     if (qz <= 0.0f) return make_float2(1e9f, 1e9f);
     // a kx qz - qx and qy - b ky qz, expanded so the O(lambda) terms cancel exactly
-    const float nx = fmaf(a * p.kx, p.dlt[2], -p.dlt[0]) + lam * fmaf(a, p.kx1, fmaf(a * p.kx, g2, -g0));
-    const float ny = fmaf(-b * p.ky, p.dlt[2], p.dlt[1]) + lam * fmaf(-b, p.ky1, fmaf(-b * p.ky, g2, g1));
+    const float bky = b * p.ky;
+    const float nx = c.nx0 + lam * fmaf(c.a, p.kx1, fmaf(c.akx, g2, -g0));
+    const float ny = fmaf(-bky, p.dlt[2], p.dlt[1]) + lam * fmaf(-b, p.ky1, fmaf(-bky, g2, g1));
     const float iq = __fdividef(1.0f, qz);
     return make_float2(p.sx * nx * iq, p.sy * ny * iq);
+}
+__device__ __forceinline__ float2 motion_at(const MotionParams &p, int x, int y) {
+    const MotionCol c = motion_col(p, x);
+    const float b = fmaf((float)y, p.by, p.b0);
+    bool ex;
+    float lam = motion_lambda(p, c, b, &ex);
+    if (ex) lam = entry_lambda_exact(p, x, y);
+    return motion_project(p, c, b, lam);
 }
 
 __global__ void __launch_bounds__(256) motion_kernel(const __grid_constant__ MotionParams p,
@@ -170,7 +206,7 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
 }
 
 // Reprojection and TAA resolve fused (Sec. 3.2): each pixel's motion is
-// computed in registers (motion_at, bitwise the motion kernel's value) instead
+// computed in registers (the motion kernel's arithmetic, bitwise) instead
 // of being written and read back; the current frame's 3x3 neighbourhoods come
 // from a shared-memory tile with a clamped one-pixel halo, copied with
 // cp.async while the motion is computed; each thread resolves two vertically
@@ -209,29 +245,43 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_ke
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // 2. motion (registers only) and the history footprint of both pixels
-    //    (rows 2 ty and 2 ty + 1 of the tile)
+    //    (rows 2 ty and 2 ty + 1 of the tile): column terms once, the two
+    //    pixels' arithmetic interleaved, the rare FP64 near-tie calls after
     bool use[2] = {false, false};
     float fxs[2] = {0.f, 0.f}, fys[2] = {0.f, 0.f};
     float4 h00[2], h01[2], h10[2], h11[2];
+    if (hist && x < W) {
+        const MotionCol col = motion_col(mp, x);
+        float bs[2], lam[2];
+        bool ex[2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int y = y0 + 2 * ty + r;
-        if (!hist || x >= W || y >= Hh) continue;
-        const float2 m = motion_at(mp, x, y);
-        const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
-        if ((m.x > xc) || (m.x < xc - (float)W) || (m.y > yc) || (m.y < yc - (float)Hh)) continue;
-        const float nx = -m.x, ny = -m.y;
-        const float flx = floorf(nx), fly = floorf(ny);
-        fxs[r] = nx - flx;
-        fys[r] = ny - fly;
-        const int ix = x + (int)flx, iy = y + (int)fly;
-        const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
-        const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
-        h00[r] = load_hist(hist, (size_t)ya * W + xa);
-        h01[r] = load_hist(hist, (size_t)ya * W + xb);
-        h10[r] = load_hist(hist, (size_t)yb * W + xa);
-        h11[r] = load_hist(hist, (size_t)yb * W + xb);
-        use[r] = true;
+        for (int r = 0; r < 2; ++r) {
+            bs[r] = fmaf((float)(y0 + 2 * ty + r), mp.by, mp.b0);
+            lam[r] = motion_lambda(mp, col, bs[r], &ex[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (ex[r]) lam[r] = entry_lambda_exact(mp, x, y0 + 2 * ty + r);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int y = y0 + 2 * ty + r;
+            if (y >= Hh) continue;
+            const float2 m = motion_project(mp, col, bs[r], lam[r]);
+            const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
+            if ((m.x > xc) || (m.x < xc - (float)W) || (m.y > yc) || (m.y < yc - (float)Hh)) continue;
+            const float nx = -m.x, ny = -m.y;
+            const float flx = floorf(nx), fly = floorf(ny);
+            fxs[r] = nx - flx;
+            fys[r] = ny - fly;
+            const int ix = x + (int)flx, iy = y + (int)fly;
+            const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
+            const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
+            h00[r] = load_hist(hist, (size_t)ya * W + xa);
+            h01[r] = load_hist(hist, (size_t)ya * W + xb);
+            h10[r] = load_hist(hist, (size_t)yb * W + xa);
+            h11[r] = load_hist(hist, (size_t)yb * W + xb);
+            use[r] = true;
+        }
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
