@@ -131,21 +131,24 @@ def march_code_sha1():
     return h.hexdigest()[:12]
 
 
-def march_traffic():
-    """DRAM bytes per march launch from the committed ncu summary, or None when
-    the kernel code has changed since those counters were taken."""
+def march_profile():
+    """Counters of the march from the committed ncu summary (DRAM bytes per
+    launch, ncu's L1TEX throughput in % of peak), or {} when the kernel code has
+    changed since they were taken."""
     h = march_code_sha1()
     prof = os.path.join(ROOT, "profiles", "march_kernel_fast-1080p.md")
     if not os.path.exists(prof):
-        return None
+        return {}
+    keys = ("code_sha1", "traffic_bytes_per_launch", "l1tex_throughput_pct")
     vals = {}
     for line in open(prof):
-        if ":" in line and line.split(":")[0] in ("code_sha1", "traffic_bytes_per_launch"):
+        if ":" in line and line.split(":")[0] in keys:
             k, v = line.split(":", 1)
             vals[k] = v.strip()
     if vals.get("code_sha1") != h:
-        return None
-    return int(vals["traffic_bytes_per_launch"])
+        return {}
+    return {"traffic": int(vals["traffic_bytes_per_launch"]),
+            "l1tex_pct": float(vals["l1tex_throughput_pct"])}
 
 
 def dist_env():
@@ -388,6 +391,7 @@ def run_gpu(args):
     sess.close()
 
     pk = _peaks()
+    mprof = march_profile()
     sm_mhz = pk["sm_max_mhz"]
     l1_peak_gbs = 152 * L1TEX_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
     # scattered 32-byte records: at most one L1 data-pipe wavefront (sector) per clock per SM
@@ -423,7 +427,8 @@ def run_gpu(args):
         "effective_lookups_per_frame": eff_lookups,
         "effective_gsamples_s": eff_lookups / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "l1tex", "achieved": achieved, "peak": l1_peak_gbs, "unit": "GB/s",
-                     "frac": achieved / l1_peak_gbs, "traffic": march_traffic(),
+                     "frac": achieved / l1_peak_gbs, "traffic": mprof.get("traffic"),
+                     "ncu_l1tex_throughput_pct_of_peak": mprof.get("l1tex_pct"),
                      "kernel": "march_kernel",
                      "peak_source": f"L1TEX data path 152 SMs x 128 B/clk x {sm_mhz:.0f} MHz "
                                     f"({pk['source']} clock)",
