@@ -121,7 +121,7 @@ def march_code_sha1():
     import re
     csrc = os.path.join(ROOT, "paper_1609_05344_gb300", "csrc")
     h = hashlib.sha1()
-    for f in ("march.cuh", "render.cu", "common.cuh"):
+    for f in ("march.cuh", "march_kernels.cuh", "render.cu", "common.cuh"):
         with open(os.path.join(csrc, f)) as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         for line in text.splitlines():
@@ -522,7 +522,8 @@ def run_batched(args):
                        "sizes": "256x256..1920x1080 seeded", "steps": "{8,16,32,128}",
                        "light_steps": 6, "volume_precision": prec,
                        "l2": "flushed between steps (256 MiB write + 256 MiB read, untimed)",
-                       "tile_shape": best, "shape_ms": times},
+                       "launch_config": best, "tile_shape_and_steps_per_iteration":
+                       list(_native.config_parts(best)), "config_ms": times},
             "ms_persistent_no_graph": res["persistent"], "ms_one_launch_per_view": res["per_view"],
             "speedup_vs_per_view": res["per_view"] / ms,
             "gpu_launches": args.steps, "clocks": dict(clk.summary(), window="all modes")}

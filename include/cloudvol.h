@@ -217,11 +217,26 @@ int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const c
                        int integration, float *out_rgba, unsigned long long *lookups,
                        void *stream);
 
-/* Times every pixel-tile shape of the raymarch on this workload (repeats
+/* Launch configurations of the raymarch that the autotuners choose from:
+ * config = shape + 4 * k, with shape the pixel tile of a 128-thread CTA (0:
+ * 16x8, 1: 32x4 of 8x4-pixel warps, 2: 32x4 of 16x2-pixel warps, 3: 8x16) and
+ * k selecting the view steps a warp evaluates per iteration of its march
+ * (0: 8, 1: 16).  Every configuration gives bitwise the same pixels. */
+#define CLOUD_TUNE_CONFIGS 8
+
+/* Times every launch configuration of the raymarch on this workload (repeats
  * launches each, writing out_rgba), remembers the fastest for the volume's
- * storage precision and light-step count (later cloud_render and new
- * batches use it), and returns it in *best (and the per-shape mean times in
- * times_ms[4] if not NULL).  Waits for the stream. */
+ * storage precision and light-step count (later cloud_render, new batches and
+ * new servers use it), and returns it in *best (and the per-configuration mean
+ * times in times_ms[CLOUD_TUNE_CONFIGS] if not NULL).  Waits for the stream. */
+/* Reads / sets the launch configuration that cloud_render, new batches and
+ * new servers use for volumes of `precision` rendered with `light_steps`
+ * light steps (e.g. to restore a configuration an earlier autotune found).
+ * config outside [0, CLOUD_TUNE_CONFIGS) or a bad precision is
+ * CLOUD_ERR_INVALID_ARG.  Process-wide; host only. */
+int cloud_get_launch_config(int precision, int light_steps, int *config);
+int cloud_set_launch_config(int precision, int light_steps, int config);
+
 int cloud_autotune_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
                           int width, int height, int steps, int light_steps, int jitter_frame,
                           int integration, float *out_rgba, int repeats, float *times_ms,
@@ -248,7 +263,8 @@ int cloud_batch_render(cloud_batch *b, void *stream);
 int cloud_batch_render_graph(cloud_batch *b, void *stream);
 /* One cloud_render launch per view (the unbatched comparison). */
 int cloud_batch_render_per_view(cloud_batch *b, void *stream);
-/* Times each tile shape for this batch and keeps the fastest (waits). */
+/* Times each launch configuration (CLOUD_TUNE_CONFIGS of them; times_ms
+ * holds that many if not NULL) for this batch and keeps the fastest (waits). */
 int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms, int *best, void *stream);
 
 /* Renders n_views views exactly as cloud_batch_create + cloud_batch_render

@@ -17,7 +17,8 @@ CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libcloudvol.so")
 HEADER = os.path.join(_ROOT, "include", "cloudvol.h")
-SOURCES = ["volume.cu", "render.cu", "batch.cu", "taa.cu", "session.cu", "server.cu"]
+SOURCES = ["volume.cu", "render.cu", "batch.cu", "march8_view.cu", "march16_view.cu",
+           "march8_batch.cu", "march16_batch.cu", "taa.cu", "session.cu", "server.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", ARCH, "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -31,6 +32,12 @@ INTEGRATION = {"analytic": 0, "basic": 1}
 HISTORY = {"fp32": 0, "fp16": 1}
 JITTER = {"pixel": 0, "frame": 1}
 MAX_LIGHT_STEPS, MAX_STEPS, MAX_DIM, MAX_VIEWS, STATIC_MAX_VIEWS = 32, 4096, 16384, 4096, 256
+TUNE_CONFIGS = 8  # launch configurations: tile shape + 4 * (view steps per iteration: 8, 16)
+
+
+def config_parts(config: int):
+    """(tile shape, view steps per warp iteration) of a launch configuration."""
+    return config % 4, (8, 16)[config // 4]
 
 
 def _nvcc() -> str:
@@ -42,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the CUDA sources for sm_103a (in parallel) and link the library."""
     os.makedirs(BUILD_DIR, exist_ok=True)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [
-        os.path.join(CSRC, h) for h in ("common.cuh", "march.cuh")] + [HEADER]
+        os.path.join(CSRC, h) for h in ("common.cuh", "march.cuh", "march_kernels.cuh")] + [HEADER]
     newest = max(os.path.getmtime(p) for p in deps)
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
@@ -151,6 +158,8 @@ SIGNATURES = [
                                        _vp, _ip, _vp]),
     ("cloud_session_wait_frame", _i, [_vp, _i, _i]),
     ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
+    ("cloud_get_launch_config", _i, [_i, _i, _P(_i)]),
+    ("cloud_set_launch_config", _i, [_i, _i, _i]),
     ("cloud_autotune_render", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, _i, _i, _i, _vp, _i,
                                    _fp, _ip, _vp]),
     ("cloud_batch_create", _i, [_vp, _P(Params), _i, _i, _P(View), _i, _P(_vp)]),

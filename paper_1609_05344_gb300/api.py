@@ -240,15 +240,31 @@ def hash4(keys: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
+def launch_config(precision: str, light_steps: int) -> int:
+    """The launch configuration renders of this precision and light-step count
+    use (cloud_get_launch_config)."""
+    c = ctypes.c_int()
+    N.check(N.lib().cloud_get_launch_config(N.PRECISION[precision], light_steps, ctypes.byref(c)),
+            "cloud_get_launch_config")
+    return c.value
+
+
+def set_launch_config(precision: str, light_steps: int, config: int):
+    """Pin the launch configuration (cloud_set_launch_config)."""
+    N.check(N.lib().cloud_set_launch_config(N.PRECISION[precision], light_steps, config),
+            "cloud_set_launch_config")
+
+
 def autotune_render(vol: Volume, cam: dict, prm: dict, width: int, height: int, steps: int,
                     light_steps: int, jitter_frame: int = -1, integration: str = "analytic",
                     repeats: int = 5, stream=None):
-    """Time every pixel-tile shape on this workload and make the fastest the
-    default for the volume's precision (cloud_autotune_render).  Returns
-    (best_shape, [ms per shape])."""
+    """Time every launch configuration (tile shape x view steps per warp
+    iteration, see _native.config_parts) on this workload and make the fastest
+    the default for the volume's precision (cloud_autotune_render).  Returns
+    (best_config, [ms per configuration])."""
     out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
     c, p = N.camera(cam), N.params(prm)
-    times = (ctypes.c_float * 4)()
+    times = (ctypes.c_float * N.TUNE_CONFIGS)()
     best = ctypes.c_int()
     N.check(N.lib().cloud_autotune_render(vol.handle, ctypes.byref(c), ctypes.byref(p), width,
                                           height, steps, light_steps, jitter_frame,
@@ -301,7 +317,9 @@ class Batch:
         return self.outputs
 
     def autotune(self, repeats: int = 3, stream=None):
-        times = (ctypes.c_float * 4)()
+        """Time every launch configuration on this batch and keep the fastest;
+        returns (best_config, [ms per configuration])."""
+        times = (ctypes.c_float * N.TUNE_CONFIGS)()
         best = ctypes.c_int()
         N.check(N.lib().cloud_batch_autotune(self._h, repeats, times, ctypes.byref(best),
                                              _stream(stream)), "cloud_batch_autotune")

@@ -19,78 +19,19 @@
 #include "march.cuh"
 
 namespace cloudvol {
-int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
-                 unsigned long long *counter, int shape, cudaStream_t s);
 
-template <typename T, int LS, int SHAPE, bool FX>
-__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
-    march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
-                       int n_views, int total_tiles, unsigned int *__restrict__ work,
-                       const T *__restrict__ base, const T *__restrict__ detail,
-                       const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
-    __shared__ WarpScratch scratch[4];
-    __shared__ ViewParams sv;
-    __shared__ int s_tile, s_view;
-    unsigned long long n_look = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const int t = (int)atomicAdd(work, 1u);
-            s_tile = t;
-            if (t < total_tiles) {
-                int lo = 0, hi = n_views - 1;  // last view with tile_begin <= t
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (views[mid].tile_begin <= t) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_view = lo;
-            }
-        }
-        __syncthreads();
-        const int t = s_tile;
-        if (t >= total_tiles) break;
-        const int *src = reinterpret_cast<const int *>(views + s_view);
-        int *dst = reinterpret_cast<int *>(&sv);
-        for (int i = threadIdx.x; i < (int)(sizeof(ViewParams) / 4); i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
-        const int local = t - sv.tile_begin;
-        n_look += march_tile<T, LS, SHAPE, FX>(p, sv, local % sv.tiles_x, local / sv.tiles_x,
-                                           scratch[threadIdx.x >> 5], base, detail, weather);
-        __syncthreads();  // s_tile / sv are rewritten by the next iteration
-    }
-    count_lookups(counter, n_look);
-}
-
-template <typename T, int SHAPE>
-static const void *batch_kernel_ptr(int light_steps, bool fx) {
-    if (fx) return (const void *)march_batch_kernel<T, 6, SHAPE, true>;
-    return light_steps == 6 ? (const void *)march_batch_kernel<T, 6, SHAPE, false>
-                            : (const void *)march_batch_kernel<T, -1, SHAPE, false>;
-}
-template <typename T>
-static const void *batch_kernel_typed(int light_steps, bool fx, int shape) {
-    switch (shape) {
-        case 1: return batch_kernel_ptr<T, 1>(light_steps, fx);
-        case 2: return batch_kernel_ptr<T, 2>(light_steps, fx);
-        case 3: return batch_kernel_ptr<T, 3>(light_steps, fx);
-        default: return batch_kernel_ptr<T, 0>(light_steps, fx);
-    }
-}
-static const void *batch_kernel(int precision, int light_steps, bool fx, int shape) {
-    switch (precision) {
-        case CLOUD_PRECISION_FP32: return batch_kernel_typed<float>(light_steps, fx, shape);
-        case CLOUD_PRECISION_FP16: return batch_kernel_typed<__half>(light_steps, fx, shape);
-        case CLOUD_PRECISION_BF16: return batch_kernel_typed<__nv_bfloat16>(light_steps, fx, shape);
-        default: return batch_kernel_typed<uint16_t>(light_steps, fx, shape);
-    }
+static const void *batch_kernel(int precision, int light_steps, bool fx, int config) {
+    return config_chunk(config) == 16
+               ? batch_kernel_ch<16>(precision, light_steps, fx, config_shape(config))
+               : batch_kernel_ch<8>(precision, light_steps, fx, config_shape(config));
 }
 
 // Enqueue counter reset + persistent kernel for the given table on stream s.
 int launch_batch(const cloud_volume *vol, const SceneParams &scene, const ViewParams *d_views,
-                 int n_views, int total_tiles, int shape, unsigned int *d_work,
+                 int n_views, int total_tiles, int config, unsigned int *d_work,
                  unsigned long long *counter, cudaStream_t s) {
     if (total_tiles == 0) return CLOUD_OK;
-    const void *fn = batch_kernel(vol->desc.precision, scene.light_steps, fixed_sizes(scene, vol), shape);
+    const void *fn = batch_kernel(vol->desc.precision, scene.light_steps, fixed_sizes(scene, vol), config);
     int dev = 0, sms = 0, per_sm = 0;
     if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
     if (int rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
@@ -117,7 +58,7 @@ struct cloud_batch {
     const cloud_volume *vol;
     cloud_params prm;
     SceneParams scene;
-    int n_views, total_tiles, shape;
+    int n_views, total_tiles, config;  // config: tile shape + view steps per iteration
     std::vector<cloud_view> views;  // caller order
     std::vector<int> order;         // queue order (decreasing steps)
     std::vector<ViewParams> table;  // queue order
@@ -143,8 +84,8 @@ void free_batch(cloud_batch *b) {
     delete b;
 }
 
-// (Re)build the view table in queue order for the batch's tile shape and
-// upload it on stream s.
+// (Re)build the view table in queue order for the batch's tile shape (from its
+// launch configuration) and upload it on stream s.
 int build_table(cloud_batch *b, cudaStream_t s) {
     b->table.resize(b->n_views);
     int next = 0;
@@ -152,7 +93,7 @@ int build_table(cloud_batch *b, cudaStream_t s) {
         const cloud_view &cv = b->views[b->order[q]];
         ViewParams &v = b->table[q];
         if (int rc = build_view(b->vol, &b->prm, &cv.camera, cv.width, cv.height, cv.steps,
-                                cv.jitter_frame, cv.out_rgba, b->shape, &v))
+                                cv.jitter_frame, cv.out_rgba, config_shape(b->config), &v))
             return rc;
         v.tile_begin = next;
         next += v.tile_count;
@@ -176,7 +117,7 @@ extern "C" int cloud_batch_create(const cloud_volume *vol, const cloud_params *p
     b->vol = vol;
     b->prm = *prm;
     b->n_views = n_views;
-    b->shape = tuned_shape(vol->desc.precision, light_steps);
+    b->config = tuned_config(vol->desc.precision, light_steps);
     b->views.assign(views, views + n_views);
     b->order.resize(n_views);
     std::iota(b->order.begin(), b->order.end(), 0);
@@ -223,7 +164,7 @@ extern "C" int cloud_batch_set_views(cloud_batch *b, const cloud_view *views, in
 extern "C" int cloud_batch_render(cloud_batch *b, void *stream) {
     clear_error();
     if (!b) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_render: null batch");
-    return launch_batch(b->vol, b->scene, b->d_views, b->n_views, b->total_tiles, b->shape,
+    return launch_batch(b->vol, b->scene, b->d_views, b->n_views, b->total_tiles, b->config,
                         b->d_work, nullptr, (cudaStream_t)stream);
 }
 
@@ -236,7 +177,7 @@ extern "C" int cloud_batch_render_graph(cloud_batch *b, void *stream) {
                             "cudaStreamBeginCapture");
         if (rc) return rc;
         const int lrc = launch_batch(b->vol, b->scene, b->d_views, b->n_views, b->total_tiles,
-                                     b->shape, b->d_work, nullptr, cs);
+                                     b->config, b->d_work, nullptr, cs);
         cudaGraph_t g = nullptr;
         rc = check_cuda(cudaStreamEndCapture(cs, &g), "cudaStreamEndCapture");
         if (lrc || rc) {
@@ -257,7 +198,7 @@ extern "C" int cloud_batch_render_per_view(cloud_batch *b, void *stream) {
     clear_error();
     if (!b) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_batch_render_per_view: null batch");
     for (int q = 0; q < b->n_views; ++q)
-        if (int rc = launch_march(b->scene, b->table[q], b->vol, nullptr, b->shape,
+        if (int rc = launch_march(b->scene, b->table[q], b->vol, nullptr, b->config,
                                   (cudaStream_t)stream))
             return rc;
     return CLOUD_OK;
@@ -275,10 +216,10 @@ extern "C" int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms
         return rc;
     }
     drop_graph(b);
-    int rc = CLOUD_OK, best_shape = 0;
+    int rc = CLOUD_OK, best_config = 0;
     float best_ms = INFINITY;
-    for (int shape = 0; shape < kShapes && !rc; ++shape) {
-        b->shape = shape;
+    for (int config = 0; config < kConfigs && !rc; ++config) {
+        b->config = config;
         rc = build_table(b, s);
         if (!rc) rc = cloud_batch_render(b, s);  // warm-up
         if (!rc) rc = check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
@@ -288,18 +229,18 @@ extern "C" int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms
         float ms = 0.0f;
         if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
         ms /= repeats;
-        if (times_ms) times_ms[shape] = ms;
+        if (times_ms) times_ms[config] = ms;
         if (!rc && ms < best_ms) {
             best_ms = ms;
-            best_shape = shape;
+            best_config = config;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    b->shape = best_shape;
+    b->config = best_config;
     if (int r2 = build_table(b, s)) return r2;
-    if (best) *best = best_shape;
+    if (best) *best = best_config;
     return CLOUD_OK;
 }
 
@@ -354,12 +295,12 @@ extern "C" int cloud_batch_render_static(const cloud_volume *vol, const cloud_pa
     for (int i = 1; i < n_views; ++i)  // stable insertion sort, longest step counts first
         for (int j = i; j > 0 && views[order[j]].steps > views[order[j - 1]].steps; --j)
             std::swap(order[j], order[j - 1]);
-    const int shape = tuned_shape(vol->desc.precision, light_steps);
+    const int config = tuned_config(vol->desc.precision, light_steps);
     int next = 0;
     for (int q = 0; q < n_views; ++q) {
         const cloud_view &cv = views[order[q]];
         if (int rc = build_view(vol, prm, &cv.camera, cv.width, cv.height, cv.steps, cv.jitter_frame,
-                                cv.out_rgba, shape, &table[q]))
+                                cv.out_rgba, config_shape(config), &table[q]))
             return rc;
         table[q].tile_begin = next;
         next += table[q].tile_count;
@@ -373,5 +314,5 @@ extern "C" int cloud_batch_render_static(const cloud_volume *vol, const cloud_pa
                                             cudaMemcpyHostToDevice, s),
                             "cloud_batch_render_static: upload view table"))
         return rc;
-    return launch_batch(vol, scene, d_views, n_views, next, shape, work, nullptr, s);
+    return launch_batch(vol, scene, d_views, n_views, next, config, work, nullptr, s);
 }

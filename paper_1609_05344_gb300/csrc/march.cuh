@@ -117,18 +117,25 @@ inline void tile_dims(int shape, int *tw, int *th) {
 }
 
 constexpr int kAxes = kLatticeAxes + 1;  // lattice axes + height above the layer bottom
-constexpr int kChunk = 8;                // view steps per warp-cooperative chunk
+// Launch configurations the autotuner chooses from: a pixel-tile shape and the
+// number of view steps a warp evaluates per iteration of its march (the chunk
+// of phase A/B/C below).  config = shape + kShapes * chunk index.
+constexpr int CHSizes[2] = {8, 16};
+constexpr int kConfigs = kShapes * 2;
+inline int config_shape(int config) { return config % kShapes; }
+inline int config_chunk(int config) { return CHSizes[(config / kShapes) & 1]; }
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Per-warp shared scratch of the march: each lane's start coordinates and
 // per-step increments, the chunk's view densities, light-march sums and the
-// list of (step, lane) pairs that need a light march.
+// list of (step, lane) pairs that need a light march (CH view steps a chunk).
+template <int CH>
 struct WarpScratch {
     uint32_t c0[kAxes][32];
     uint32_t e[kAxes][32];
-    float rho[kChunk][32];
-    float lsum[kChunk][32];
-    uint16_t pairs[kChunk * 32];
+    float rho[CH][32];
+    float lsum[CH][32];
+    uint16_t pairs[CH * 32];
 };
 
 __device__ __forceinline__ float frac23(uint32_t f) {
@@ -217,7 +224,7 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 }
 
 // The march of one CTA pixel tile (4 warps, one pixel per lane).  View steps
-// are processed in chunks of kChunk:
+// are processed in chunks of CH:
 //   A  each lane evaluates its view densities and its early out (the optical
 //      depth does not depend on the lighting);
 //   B  the warp shares out every (step, lane) light march with density > 0
@@ -226,9 +233,9 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 //   C  each lane integrates its steps in order with the light sums from B.
 // The arithmetic of every sample is the same as a per-lane march.  Returns the
 // number of density lookups this lane performed.
-template <typename T, int LS, int SHAPE, bool FX>
+template <typename T, int LS, int SHAPE, bool FX, int CH>
 __device__ __forceinline__ unsigned long long march_tile(
-    const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch &ws,
+    const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch<CH> &ws,
     const T *__restrict__ base, const T *__restrict__ detail, const T *__restrict__ weather) {
     using S = TileShape<SHAPE>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -327,14 +334,14 @@ __device__ __forceinline__ unsigned long long march_tile(
     ws.e[kLatticeAxes][lane] = (uint32_t)eh;
     const unsigned lt_mask = (1u << lane) - 1u;
     float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    for (int i0 = 0; i0 < v.steps && __any_sync(kFull, alive); i0 += kChunk) {
+    for (int i0 = 0; i0 < v.steps && __any_sync(kFull, alive); i0 += CH) {
         // --- A: view densities and early out --------------------------------
         uint32_t act = 0;
         int nA = 0;
         if (alive) {
             float tau_a = tau;
 #pragma unroll 1
-            for (int k = 0; k < kChunk; ++k) {
+            for (int k = 0; k < CH; ++k) {
                 if (i0 + k >= v.steps) break;
                 // --- a3: density lookup ---------------------------------------
                 const float rho = density<FX>(p, base, detail, weather, c, hq);
@@ -357,16 +364,16 @@ __device__ __forceinline__ unsigned long long march_tile(
         }
         if (!__any_sync(kFull, act != 0u)) continue;  // no density in this chunk, warp-wide
         // --- B: light marches shared out over the warp (a4, Sec. 1) ----------
-        unsigned offs[kChunk + 1];
+        unsigned offs[CH + 1];
         offs[0] = 0;
 #pragma unroll
-        for (int k = 0; k < kChunk; ++k) {
+        for (int k = 0; k < CH; ++k) {
             const unsigned m = __ballot_sync(kFull, (act >> k) & 1u);
             if ((act >> k) & 1u) ws.pairs[offs[k] + __popc(m & lt_mask)] = (uint16_t)((k << 5) | lane);
             offs[k + 1] = offs[k] + __popc(m);
         }
         __syncwarp();
-        for (unsigned q = lane; q < offs[kChunk]; q += 32) {
+        for (unsigned q = lane; q < offs[CH]; q += 32) {
             const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
             const uint32_t i = (uint32_t)(i0 + (int)k);
             uint32_t cs[kLatticeAxes];
@@ -428,7 +435,18 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
                 SceneParams *p);
 int build_view(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *cam, int width,
                int height, int steps, int jitter_frame, float *out, int shape, ViewParams *v);
-int tuned_shape(int precision, int light_steps);
+// The autotuned launch configuration for (storage precision, light steps).
+int tuned_config(int precision, int light_steps);
+// Raymarch of one view with the given configuration (render.cu); the
+// per-chunk-size kernels and their dispatch are instantiated in
+// march{8,16}_{view,batch}.cu.
+int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
+                 unsigned long long *counter, int config, cudaStream_t s);
+template <int CH>
+void launch_march_ch(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
+                     unsigned long long *counter, int shape, cudaStream_t s);
+template <int CH>
+const void *batch_kernel_ch(int precision, int light_steps, bool fx, int shape);
 // True when a launch can use the FX march: the standard tile sizes, all three
 // tiles present, noise density and six light steps.
 bool fixed_sizes(const SceneParams &p, const cloud_volume *vol);

@@ -4,25 +4,14 @@
 // One thread per pixel; a 128-thread CTA covers one pixel tile (shape chosen
 // by the autotuner, 16x8 by default) so the rays of a warp stay adjacent and
 // touch the same region of the L2-resident noise tiles.  The device code is
-// in march.cuh.
+// in march.cuh, the kernels in march_kernels.cuh (instantiated by
+// march{8,16}_{view,batch}.cu).
 #include <cmath>
 #include <mutex>
 
 #include "march.cuh"
 
 namespace cloudvol {
-
-template <typename T, int LS, int SHAPE, bool FX>
-__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
-    march_kernel(const __grid_constant__ SceneParams p, const __grid_constant__ ViewParams v,
-                 const T *__restrict__ base, const T *__restrict__ detail,
-                 const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
-    __shared__ WarpScratch scratch[4];
-    const unsigned long long n =
-        march_tile<T, LS, SHAPE, FX>(p, v, blockIdx.x, blockIdx.y, scratch[threadIdx.x >> 5], base,
-                                 detail, weather);
-    count_lookups(counter, n);
-}
 
 static double dot3(const double a[3], const double b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -154,21 +143,22 @@ int build_view(const cloud_volume *vol, const cloud_params *prm, const cloud_cam
 }
 
 // ---------------------------------------------------------------------------
-// Tile-shape selection: the autotuner records the fastest shape per (storage
-// precision, light-step specialisation); launches use it when present.
+// Launch-configuration selection: the autotuner records the fastest (tile
+// shape, view steps per warp iteration) per (storage precision, light-step
+// specialisation); launches use it when present.
 namespace {
 std::mutex g_tune_mu;
-int g_best_shape[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
+int g_best_config[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
 }  // namespace
 
-int tuned_shape(int precision, int light_steps) {
+int tuned_config(int precision, int light_steps) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    const int s = g_best_shape[precision & 3][light_steps == 6 ? 1 : 0];
-    return s < 0 ? 0 : s;
+    const int c = g_best_config[precision & 3][light_steps == 6 ? 1 : 0];
+    return c < 0 ? 0 : c;
 }
-void set_tuned_shape(int precision, int light_steps, int shape) {
+void set_tuned_config(int precision, int light_steps, int config) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_best_shape[precision & 3][light_steps == 6 ? 1 : 0] = shape;
+    g_best_config[precision & 3][light_steps == 6 ? 1 : 0] = config;
 }
 
 bool fixed_sizes(const SceneParams &p, const cloud_volume *vol) {
@@ -177,40 +167,12 @@ bool fixed_sizes(const SceneParams &p, const cloud_volume *vol) {
            p.log2_weather == kStdLog2Weather;
 }
 
-template <typename T, int SHAPE>
-static void launch_shape(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
-                         unsigned long long *counter, cudaStream_t s) {
-    int tw, th;
-    tile_dims(SHAPE, &tw, &th);
-    const dim3 grid(v.tiles_x, (v.height + th - 1) / th);
-    const T *b = (const T *)vol->base, *d = (const T *)vol->detail, *w = (const T *)vol->weather;
-    if (fixed_sizes(p, vol))
-        march_kernel<T, 6, SHAPE, true><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
-    else if (p.light_steps == 6)
-        march_kernel<T, 6, SHAPE, false><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
-    else
-        march_kernel<T, -1, SHAPE, false><<<grid, 128, 0, s>>>(p, v, b, d, w, counter);
-}
-
-template <typename T>
-static void launch_typed(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
-                         unsigned long long *counter, int shape, cudaStream_t s) {
-    switch (shape) {
-        case 1: launch_shape<T, 1>(p, v, vol, counter, s); break;
-        case 2: launch_shape<T, 2>(p, v, vol, counter, s); break;
-        case 3: launch_shape<T, 3>(p, v, vol, counter, s); break;
-        default: launch_shape<T, 0>(p, v, vol, counter, s);
-    }
-}
-
 int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
-                 unsigned long long *counter, int shape, cudaStream_t s) {
-    switch (vol->desc.precision) {
-        case CLOUD_PRECISION_FP32: launch_typed<float>(p, v, vol, counter, shape, s); break;
-        case CLOUD_PRECISION_FP16: launch_typed<__half>(p, v, vol, counter, shape, s); break;
-        case CLOUD_PRECISION_BF16: launch_typed<__nv_bfloat16>(p, v, vol, counter, shape, s); break;
-        default: launch_typed<uint16_t>(p, v, vol, counter, shape, s);
-    }
+                 unsigned long long *counter, int config, cudaStream_t s) {
+    if (config_chunk(config) == 16)
+        launch_march_ch<16>(p, v, vol, counter, config_shape(config), s);
+    else
+        launch_march_ch<8>(p, v, vol, counter, config_shape(config), s);
     return check_launch("march_kernel");
 }
 
@@ -223,11 +185,12 @@ int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_render: counter not 8-byte aligned");
     SceneParams p;
     ViewParams v;
-    const int shape = tuned_shape(vol->desc.precision, light_steps);
+    const int config = tuned_config(vol->desc.precision, light_steps);
     if (int rc = build_scene(vol, prm, light_steps, integration, &p)) return rc;
-    if (int rc = build_view(vol, prm, cam, width, height, steps, jitter_frame, out, shape, &v))
+    if (int rc = build_view(vol, prm, cam, width, height, steps, jitter_frame, out,
+                            config_shape(config), &v))
         return rc;
-    return launch_march(p, v, vol, counter, shape, s);
+    return launch_march(p, v, vol, counter, config, s);
 }
 
 }  // namespace cloudvol
@@ -270,30 +233,48 @@ extern "C" int cloud_autotune_render(const cloud_volume *vol, const cloud_camera
         cudaEventDestroy(e0);
         return rc;
     }
-    int best_shape = 0, rc = CLOUD_OK;
+    int best_config = 0, rc = CLOUD_OK;
     float best_ms = INFINITY;
-    for (int shape = 0; shape < kShapes && !rc; ++shape) {
+    for (int config = 0; config < kConfigs && !rc; ++config) {
         ViewParams v;
-        rc = build_view(vol, prm, cam, width, height, steps, jitter_frame, out_rgba, shape, &v);
+        rc = build_view(vol, prm, cam, width, height, steps, jitter_frame, out_rgba,
+                        config_shape(config), &v);
         if (rc) break;
-        rc = launch_march(p, v, vol, nullptr, shape, s);  // warm-up
+        rc = launch_march(p, v, vol, nullptr, config, s);  // warm-up
         if (!rc) rc = check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
-        for (int r = 0; r < repeats && !rc; ++r) rc = launch_march(p, v, vol, nullptr, shape, s);
+        for (int r = 0; r < repeats && !rc; ++r) rc = launch_march(p, v, vol, nullptr, config, s);
         if (!rc) rc = check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
         if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
         float ms = 0.0f;
         if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
         ms /= repeats;
-        if (times_ms) times_ms[shape] = ms;
+        if (times_ms) times_ms[config] = ms;
         if (!rc && ms < best_ms) {
             best_ms = ms;
-            best_shape = shape;
+            best_config = config;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    set_tuned_shape(vol->desc.precision, light_steps, best_shape);
-    if (best) *best = best_shape;
+    set_tuned_config(vol->desc.precision, light_steps, best_config);
+    if (best) *best = best_config;
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_get_launch_config(int precision, int light_steps, int *config) {
+    clear_error();
+    if (!config || precision < CLOUD_PRECISION_FP32 || precision > CLOUD_PRECISION_UNORM16)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_get_launch_config: bad arguments");
+    *config = tuned_config(precision, light_steps);
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_set_launch_config(int precision, int light_steps, int config) {
+    clear_error();
+    if (precision < CLOUD_PRECISION_FP32 || precision > CLOUD_PRECISION_UNORM16 || config < 0 ||
+        config >= kConfigs)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_set_launch_config: bad arguments");
+    set_tuned_config(precision, light_steps, config);
     return CLOUD_OK;
 }

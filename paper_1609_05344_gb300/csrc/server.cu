@@ -31,7 +31,7 @@
 
 namespace cloudvol {
 int launch_batch(const cloud_volume *vol, const SceneParams &scene, const ViewParams *d_views,
-                 int n_views, int total_tiles, int shape, unsigned int *d_work,
+                 int n_views, int total_tiles, int config, unsigned int *d_work,
                  unsigned long long *counter, cudaStream_t s);
 int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                          const cloud_camera *cur, const void *history, const float *current,
@@ -89,7 +89,7 @@ struct cloud_server {
     SceneParams scene{};
     cloud_server_config cfg{};
     int device = 0;
-    int shape = 0;
+    int config = 0;  // launch configuration (tile shape, view steps per iteration)
     std::mutex mu;
     std::condition_variable cv;
     std::vector<Session> sessions;
@@ -152,7 +152,7 @@ int launch_slot(cloud_server *srv, int si, const std::vector<Request *> &batch) 
         const Session &se = srv->sessions[r.session];
         ViewParams &v = sl.h_table[q];
         if (int rc = build_view(srv->vol, &srv->prm, &r.cam, se.width, se.height, r.steps, se.frame,
-                                se.current, srv->shape, &v))
+                                se.current, config_shape(srv->config), &v))
             return rc;
         v.tile_begin = next;
         next += v.tile_count;
@@ -161,7 +161,7 @@ int launch_slot(cloud_server *srv, int si, const std::vector<Request *> &batch) 
                                             cudaMemcpyHostToDevice, sl.stream),
                             "server: upload view table"))
         return rc;
-    if (int rc = launch_batch(srv->vol, srv->scene, sl.d_table, n, next, srv->shape, sl.d_work,
+    if (int rc = launch_batch(srv->vol, srv->scene, sl.d_table, n, next, srv->config, sl.d_work,
                               nullptr, sl.stream))
         return rc;
     for (const Request *rp : batch) {
@@ -279,7 +279,7 @@ extern "C" int cloud_server_create(const cloud_volume *vol, const cloud_params *
     srv->cfg = *cfg;
     int rc = check_cuda(cudaGetDevice(&srv->device), "cudaGetDevice");
     if (!rc) rc = build_scene(vol, prm, light_steps, CLOUD_INTEGRATE_ANALYTIC, &srv->scene);
-    srv->shape = tuned_shape(vol->desc.precision, light_steps);
+    srv->config = tuned_config(vol->desc.precision, light_steps);
     srv->sessions.resize(cfg->max_sessions);
     srv->slots.resize(cfg->slots);
     for (auto &sl : srv->slots) {
