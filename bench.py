@@ -373,20 +373,24 @@ def run_gpu(args):
     # end to end through the session API: every step renders, resolves and reads its
     # resolved frame back into pinned host memory (33 MB); the read-back of frame k runs on
     # the session's copy stream while frame k+1 renders (three host buffers in rotation)
+    # (at least 64 frames, so that filling and draining the two-frame pipeline is a
+    # small share; the host-side camera descriptions are prepared before the clock)
     hosts = [torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True) for _ in range(3)]
     sess = api.Session(vol, W, H, "fp32")
     for f in range(args.warmup):
         sess.wait_frame(sess.frame_async(cam(f), prm, S, LS, hosts[f % 3]))
+    n_e2e = max(args.steps, 64)
+    cams_e2e = [cam(fi + k) for k in range(n_e2e)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pending = []
-    for k in range(args.steps):
-        pending.append(sess.frame_async(cam(fi + k), prm, S, LS, hosts[k % 3]))
+    for k in range(n_e2e):
+        pending.append(sess.frame_async(cams_e2e[k], prm, S, LS, hosts[k % 3]))
         if len(pending) > 2:
             sess.wait_frame(pending.pop(0))
     for idx in pending:
         sess.wait_frame(idx)
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = (time.perf_counter() - t0) / n_e2e
     e2e_value, _ = aggregate(e2e_s * 1e3, samples, world, reduce_max)
     sess.close()
 
@@ -439,7 +443,7 @@ def run_gpu(args):
                          "frac": taa_gbs / pk["hbm_gbs"], "bytes_per_pixel": taa_bytes_px,
                          "kernel": "taa_reproject_kernel",
                          "peak_source": pk["source"]},
-        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_s * 1e3, "frames": n_e2e,
                 "h2d_bytes_per_step": 216, "d2h_bytes_per_step": W * H * 16,
                 "api": "cloud_session_frame_async + cloud_session_wait_frame (read-back "
                        "overlapped with the next frame)"},

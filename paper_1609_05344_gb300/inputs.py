@@ -13,6 +13,7 @@ cloud layer seen from the ground, and a moving camera for TAA.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -78,10 +79,15 @@ def ground_camera() -> dict:
     return camera((0.0, 0.0, 500.0), 0.0, 20.0, 60.0)
 
 
+@functools.lru_cache(maxsize=None)
+def _orbit_start(seed: int) -> float:
+    return float(np.random.default_rng(seed).uniform(0.0, 360.0))
+
+
 def orbit_camera(frame: int, seed: int = 3) -> dict:
     """Seeded orbit: radius 3 km at 500 m height, facing the centre, pitched
     12 degrees up; the orbit angle advances 0.25 degrees per frame."""
-    start = float(np.random.default_rng(seed).uniform(0.0, 360.0))
+    start = _orbit_start(seed)
     phi = start + 0.25 * frame
     pos = (3000.0 * math.cos(math.radians(phi)), 3000.0 * math.sin(math.radians(phi)), 500.0)
     return camera(pos, phi + 180.0, 12.0, 60.0)
