@@ -22,11 +22,40 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
-def _require_cuda(t: torch.Tensor, name: str, dtype=None):
-    if not t.is_cuda or not t.is_contiguous():
+def _require_cuda(t: torch.Tensor, name: str, dtype=None, shape=None):
+    """A kernel reads or writes exactly the elements its sizes imply, on the
+    current device: anything else is refused here, before a launch."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
-    if dtype is not None and t.dtype != dtype:
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
         raise ValueError(f"{name} must be {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+
+
+class _DeviceArray:
+    """A library-owned device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 2, "strides": None}
+
+
+def _device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
+    """Zero-copy tensor view of a library-owned device buffer (valid as long as
+    the library keeps that buffer)."""
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+def _require_host(t, name: str, nbytes: int):
+    """A host buffer the library copies exactly nbytes into."""
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CPU tensor (pinned for asynchronous copies)")
+    if t.numel() * t.element_size() != nbytes:
+        raise ValueError(f"{name} must hold exactly {nbytes} bytes")
 
 
 class Volume:
@@ -84,9 +113,7 @@ def render(vol: Volume, cam: dict, prm: dict, width: int, height: int, steps: in
     lookups the launch executed (a 1-element int64 CUDA tensor)."""
     if out is None:
         out = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
-    _require_cuda(out, "out", torch.float32)
-    if out.numel() != width * height * 4:
-        raise ValueError("out has the wrong size")
+    _require_cuda(out, "out", torch.float32, (height, width, 4))
     c, p = N.camera(cam), N.params(prm)
     if count:
         ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -106,7 +133,7 @@ def motion(vol: Volume, prm: dict, prev: dict, cur: dict, width: int, height: in
     """Per-pixel reprojection motion (cloud_motion): (H, W, 2) float32."""
     if out is None:
         out = torch.empty((height, width, 2), dtype=torch.float32, device="cuda")
-    _require_cuda(out, "out", torch.float32)
+    _require_cuda(out, "out", torch.float32, (height, width, 2))
     a, b, p = N.camera(prev), N.camera(cur), N.params(prm)
     N.check(N.lib().cloud_motion(vol.handle, ctypes.byref(p), ctypes.byref(a), ctypes.byref(b),
                                  width, height, _ptr(out), _stream(stream)), "cloud_motion")
@@ -117,15 +144,17 @@ def taa(history, current: torch.Tensor, motion_px: torch.Tensor, blend: float = 
         history_fmt: str = "fp32", stream=None):
     """TAA resolve (taa_resolve).  history None means the first frame.
     history/out are float32 (H, W, 4) or float16 (H, W, 4) per history_fmt."""
+    _require_cuda(current, "current", torch.float32)
+    if current.dim() != 3 or current.shape[2] != 4:
+        raise ValueError("current must have shape (H, W, 4)")
     h, w = current.shape[:2]
     dt = torch.float32 if history_fmt == "fp32" else torch.float16
     if out is None:
         out = torch.empty((h, w, 4), dtype=dt, device="cuda")
-    _require_cuda(current, "current", torch.float32)
-    _require_cuda(motion_px, "motion", torch.float32)
-    _require_cuda(out, "out", dt)
+    _require_cuda(motion_px, "motion", torch.float32, (h, w, 2))
+    _require_cuda(out, "out", dt, (h, w, 4))
     if history is not None:
-        _require_cuda(history, "history", dt)
+        _require_cuda(history, "history", dt, (h, w, 4))
     N.check(N.lib().taa_resolve(_ptr(history), _ptr(current), _ptr(motion_px), _ptr(out), w, h,
                                 N.HISTORY[history_fmt], float(blend), _stream(stream)),
             "taa_resolve")
@@ -136,14 +165,16 @@ def taa_reproject(vol: Volume, prm: dict, prev, cur: dict, history, current: tor
                   blend: float = 0.1, out=None, history_fmt: str = "fp32", stream=None):
     """Motion (prev -> cur) and TAA resolve fused (cloud_taa_reproject); history
     None is a first frame."""
+    _require_cuda(current, "current", torch.float32)
+    if current.dim() != 3 or current.shape[2] != 4:
+        raise ValueError("current must have shape (H, W, 4)")
     h, w = current.shape[:2]
     dt = torch.float32 if history_fmt == "fp32" else torch.float16
     if out is None:
         out = torch.empty((h, w, 4), dtype=dt, device="cuda")
-    _require_cuda(current, "current", torch.float32)
-    _require_cuda(out, "out", dt)
+    _require_cuda(out, "out", dt, (h, w, 4))
     if history is not None:
-        _require_cuda(history, "history", dt)
+        _require_cuda(history, "history", dt, (h, w, 4))
     pc = N.camera(prev) if prev is not None else None
     c, p = N.camera(cur), N.params(prm)
     N.check(N.lib().cloud_taa_reproject(vol.handle, ctypes.byref(p),
@@ -157,12 +188,15 @@ def taa_reproject(vol: Volume, prm: dict, prev, cur: dict, history, current: tor
 def composite(cloud: torch.Tensor, background: torch.Tensor, out=None, stream=None):
     """Upsample the premultiplied cloud buffer (float32 or float16 (h, w, 4)) to
     the background's size and lay it over the background (cloud_composite)."""
-    _require_cuda(cloud, "cloud")
+    _require_cuda(cloud, "cloud", (torch.float32, torch.float16))
     _require_cuda(background, "background", torch.float32)
+    if cloud.dim() != 3 or cloud.shape[2] != 4 or background.dim() != 3 or background.shape[2] != 4:
+        raise ValueError("cloud and background must have shape (H, W, 4)")
     fmt = "fp32" if cloud.dtype == torch.float32 else "fp16"
     h, w = background.shape[:2]
     if out is None:
         out = torch.empty_like(background)
+    _require_cuda(out, "out", torch.float32, (h, w, 4))
     N.check(N.lib().cloud_composite(_ptr(cloud), N.HISTORY[fmt], cloud.shape[1], cloud.shape[0],
                                     _ptr(background), _ptr(out), w, h, _stream(stream)),
             "cloud_composite")
@@ -193,10 +227,14 @@ class Session:
     def reset(self):
         N.check(N.lib().cloud_session_reset(self._h), "cloud_session_reset")
 
+    def _frame_bytes(self) -> int:
+        return self.width * self.height * (16 if self.history_fmt == "fp32" else 8)
+
     def frame_async(self, cam: dict, prm: dict, steps: int, light_steps: int, host_out,
                     blend: float = 0.1, integration: str = "analytic", stream=None) -> int:
         """Render + resolve one frame and start copying it into host_out on the
         session's copy stream; returns the frame index to pass to wait_frame."""
+        _require_host(host_out, "host_out", self._frame_bytes())
         c, p = N.camera(cam), N.params(prm)
         idx = ctypes.c_int()
         N.check(N.lib().cloud_session_frame_async(self._h, ctypes.byref(c), ctypes.byref(p), steps,
@@ -216,6 +254,8 @@ class Session:
         tensor of H*W*4 elements) the resolved frame is copied there and the
         call waits; otherwise returns a CUDA tensor view of the resolved frame
         (valid until the next frame)."""
+        if host_out is not None:
+            _require_host(host_out, "host_out", self._frame_bytes())
         c, p = N.camera(cam), N.params(prm)
         dev = ctypes.c_void_p()
         hp = ctypes.c_void_p(host_out.data_ptr()) if host_out is not None else ctypes.c_void_p()
@@ -225,7 +265,8 @@ class Session:
                 "cloud_session_frame")
         if host_out is not None:
             return host_out
-        return dev.value
+        return _device_view(dev.value, (self.height, self.width, 4),
+                            "<f4" if self.history_fmt == "fp32" else "<f2")
 
 
 def hash4(keys: torch.Tensor, stream=None) -> torch.Tensor:

@@ -161,3 +161,34 @@ def test_composite_parity(api, oracle, src, dst, fmt):
     got = api.composite(_t(cloud), _t(bg)).cpu().numpy()
     ref = oracle.composite(cloud.astype(np.float64), bg.astype(np.float64))
     assert np.abs(got - ref).max() <= 1e-5
+
+
+def test_session_frame_device_view_and_buffer_checks(api):
+    """Without host_out a session frame is a zero-copy view of the resolved
+    history; mis-sized or device-side host buffers are refused before any launch."""
+    import torch
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    prm = I.params()
+    for fmt, dt in (("fp32", torch.float32), ("fp16", torch.float16)):
+        sess = api.Session(vol, 64, 48, fmt)
+        host = torch.empty((48, 64, 4), dtype=dt, pin_memory=True)
+        sess.frame(I.orbit_camera(0, 3), prm, 8, 6, host_out=host)
+        view = sess.frame(I.orbit_camera(1, 3), prm, 8, 6)
+        assert view.is_cuda and view.dtype == dt and tuple(view.shape) == (48, 64, 4)
+        torch.cuda.synchronize()
+        got = view.cpu().numpy().copy()
+        ref = api.Session(vol, 64, 48, fmt)
+        ref.frame(I.orbit_camera(0, 3), prm, 8, 6, host_out=host)
+        ref.frame(I.orbit_camera(1, 3), prm, 8, 6, host_out=host)
+        assert np.array_equal(got, host.numpy())
+        with pytest.raises(ValueError):
+            sess.frame(I.orbit_camera(2, 3), prm, 8, 6, host_out=torch.empty(10, dtype=dt))
+        with pytest.raises(ValueError):
+            sess.frame(I.orbit_camera(2, 3), prm, 8, 6, host_out=view)
+        sess.close()
+        ref.close()
+    with pytest.raises(ValueError):
+        api.render(vol, I.orbit_camera(0, 3), prm, 64, 48, 8, 6,
+                   out=torch.empty((48, 63, 4), device="cuda"))
+    with pytest.raises(ValueError):
+        api.taa(None, torch.empty((48, 64, 4), device="cuda"), torch.empty((48, 64, 1), device="cuda"))
