@@ -446,7 +446,10 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_s * 1e3, "frames": n_e2e,
                 "h2d_bytes_per_step": 216, "d2h_bytes_per_step": W * H * 16,
                 "api": "cloud_session_frame_async + cloud_session_wait_frame (read-back "
-                       "overlapped with the next frame)"},
+                       "overlapped with the next frame)",
+                "l2": "not flushed: frames back to back through the session API, as an "
+                      "application runs them (wall clock over all frames incl. pipeline "
+                      "fill and drain)"},
         "gpu_launches": launches,
         "clocks": dict(clk.summary(), window="warm-up and timed frames"),
     }
