@@ -168,6 +168,10 @@ inline void split_df10(double v, float *hi, float *lo) {
 // The loaders return the corners in an affine "raw" form r = texel + bias so
 // that a 16-bit fixed-point texel decodes with bit operations only; the
 // interpolated raw value minus `raw_bias<T>()` is the centred texel value.
+// They return the dx = 1 half of a record as differences from the dx = 0 half
+// (c[r + R/2] - c[r]), the operand the x lerp needs: FP32 records store them
+// so (packed once, rounded exactly as the lerp would), 16-bit loaders form
+// them after decoding.
 template <typename T>
 __host__ __device__ constexpr float raw_bias() { return 0.0f; }
 template <>
@@ -202,6 +206,9 @@ __device__ __forceinline__ void load_rec8(const T *tile, uint32_t rec, float c[8
     unpack16(r.y, tile, c[2], c[3]);
     unpack16(r.z, tile, c[4], c[5]);
     unpack16(r.w, tile, c[6], c[7]);
+    const float2 d0 = __fadd2_rn(make_float2(c[4], c[5]), make_float2(-c[0], -c[1]));
+    const float2 d1 = __fadd2_rn(make_float2(c[6], c[7]), make_float2(-c[2], -c[3]));
+    c[4] = d0.x; c[5] = d0.y; c[6] = d1.x; c[7] = d1.y;
 }
 __device__ __forceinline__ void load_rec4(const float *tile, uint32_t rec, float c[4]) {
     const float4 a = __ldg(reinterpret_cast<const float4 *>(tile) + rec);
@@ -212,6 +219,8 @@ __device__ __forceinline__ void load_rec4(const T *tile, uint32_t rec, float c[4
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(tile) + rec);
     unpack16(r.x, tile, c[0], c[1]);
     unpack16(r.y, tile, c[2], c[3]);
+    const float2 d = __fadd2_rn(make_float2(c[2], c[3]), make_float2(-c[0], -c[1]));
+    c[2] = d.x; c[3] = d.y;
 }
 
 // Plain (unpacked) texel loads, decoded to the centred value.

@@ -153,23 +153,24 @@ __device__ __forceinline__ uint32_t rec2(int L, uint32_t cx, uint32_t cy) {
     return ((cy >> sh) << L) | (cx >> sh);
 }
 // Interpolation on packed FP32x2 (Blackwell FFMA2/FADD2): x first on the
-// (z0, z1) pairs of both y rows, then y on the pair, then z.  Each lane of a
-// packed op rounds exactly like the scalar op.
+// (z0, z1) pairs of both y rows (the x differences come with the record),
+// then y on the pair, then z.  Each lane of a packed op rounds exactly like
+// the scalar op.
 __device__ __forceinline__ float trilerp(const float c[8], int L, uint32_t cx, uint32_t cy,
                                          uint32_t cz) {
     const float fx = frac23(cx << L), fy = frac23(cy << L), fz = frac23(cz << L);
     const float2 a0 = make_float2(c[0], c[1]), a1 = make_float2(c[2], c[3]);  // dx = 0
-    const float2 b0 = make_float2(c[4], c[5]), b1 = make_float2(c[6], c[7]);  // dx = 1
+    const float2 d0 = make_float2(c[4], c[5]), d1 = make_float2(c[6], c[7]);  // dx = 1 minus dx = 0
     const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
-    const float2 x0 = __ffma2_rn(fx2, __fadd2_rn(b0, make_float2(-a0.x, -a0.y)), a0);  // dy = 0
-    const float2 x1 = __ffma2_rn(fx2, __fadd2_rn(b1, make_float2(-a1.x, -a1.y)), a1);  // dy = 1
+    const float2 x0 = __ffma2_rn(fx2, d0, a0);  // dy = 0
+    const float2 x1 = __ffma2_rn(fx2, d1, a1);  // dy = 1
     const float2 yz = __ffma2_rn(fy2, __fadd2_rn(x1, make_float2(-x0.x, -x0.y)), x0);  // (z0, z1)
     return fmaf(fz, yz.y - yz.x, yz.x);
 }
 __device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, uint32_t cy) {
     const float fx = frac23(cx << L), fy = frac23(cy << L);
-    const float2 a = make_float2(c[0], c[1]), b = make_float2(c[2], c[3]);  // (y0, y1) at dx
-    const float2 xy = __ffma2_rn(make_float2(fx, fx), __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
+    const float2 a = make_float2(c[0], c[1]), d = make_float2(c[2], c[3]);  // (y0, y1): dx = 0, difference
+    const float2 xy = __ffma2_rn(make_float2(fx, fx), d, a);
     return fmaf(fy, xy.y - xy.x, xy.x);
 }
 

@@ -128,6 +128,23 @@ __global__ void fbm2_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint3
 }
 
 // Corner-packing of a generated tile (see common.cuh).
+// Record layout (see common.cuh): the dx = 0 half of a record holds texels,
+// the dx = 1 half holds them as differences from the dx = 0 half for FP32
+// tiles (rounded exactly as the lerp would round them) and as texels for
+// 16-bit tiles (whose loaders form the differences after decoding).
+template <typename T, int R>
+__device__ __forceinline__ void store_record(T *dst, const T (&t)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r] = t[r];
+}
+template <int R>
+__device__ __forceinline__ void store_record(float *dst, const float (&t)[R]) {
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) dst[r] = t[r];
+#pragma unroll
+    for (int r = R / 2; r < R; ++r) dst[r] = __fsub_rn(t[r], t[r - R / 2]);
+}
+
 template <typename T>
 __global__ void pack3_kernel(const T *__restrict__ plain, T *__restrict__ packed, int log2n) {
     const uint32_t mask = (1u << log2n) - 1u;
@@ -136,12 +153,14 @@ __global__ void pack3_kernel(const T *__restrict__ plain, T *__restrict__ packed
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n) & mask,
                        z = (uint32_t)(i >> (2 * log2n));
+        T t[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {  // r = 4 dx + 2 dy + dz
             const uint32_t xx = (x + (r >> 2)) & mask, yy = (y + ((r >> 1) & 1)) & mask,
                            zz = (z + (r & 1)) & mask;
-            packed[8 * i + r] = plain[((uint64_t)zz << (2 * log2n)) | (yy << log2n) | xx];
+            t[r] = plain[((uint64_t)zz << (2 * log2n)) | (yy << log2n) | xx];
         }
+        store_record(packed + 8 * i, t);
     }
 }
 
@@ -152,11 +171,13 @@ __global__ void pack2_kernel(const T *__restrict__ plain, T *__restrict__ packed
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n);
+        T t[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {  // r = 2 dx + dy
             const uint32_t xx = (x + (r >> 1)) & mask, yy = (y + (r & 1)) & mask;
-            packed[4 * i + r] = plain[(yy << log2n) | xx];
+            t[r] = plain[(yy << log2n) | xx];
         }
+        store_record(packed + 4 * i, t);
     }
 }
 
