@@ -199,12 +199,19 @@ def cpu_baseline(wl, prm, budget_s=12.0, gpu_frame=None):
             break
     dt = time.perf_counter() - t0
     samples = wl.width * wl.height * wl.steps * (1 + wl.light_steps) * frames
+    # one thread: the raymarch of one frame (the bulk of the oracle's work)
+    t1 = time.perf_counter()
+    O.render(ovol, I.orbit_camera(0, wl.volume["seed"]), prm, wl.width, wl.height, wl.steps,
+             wl.light_steps, jitter_frame=0, nthreads=1)
+    dt1 = time.perf_counter() - t1
     err = None
     if gpu_frame is not None:
         err = float(np.abs(gpu_frame.astype(np.float64) - first_img).max())
     return {"value": samples / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{frames} whole frame(s) of the workload (render+motion+TAA), FP64, "
-                      f"{cores} threads, {dt:.1f} s"}, err
+                      f"{cores} threads, {dt:.1f} s",
+            "single_thread": {"value": wl.width * wl.height * wl.steps * (1 + wl.light_steps) / dt1 / 1e9,
+                              "unit": UNIT, "sample": f"the raymarch of one frame, 1 thread, {dt1:.1f} s"}}, err
 
 
 def run_reference(args):
