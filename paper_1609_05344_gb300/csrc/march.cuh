@@ -18,12 +18,6 @@
 
 #include "common.cuh"
 
-// 1: fetch the detail record only after the base shows B > c (fewer L1 sectors,
-// one more dependent memory round trip); 0: fetch all records of a lookup at once.
-#ifndef CLOUDVOL_DETAIL_AFTER_BASE
-#define CLOUDVOL_DETAIL_AFTER_BASE 0
-#endif
-
 // CTAs per SM the march is compiled for (register budget 65536 / (128 x this)),
 // for FP32 records and for 16-bit records (which need fewer registers).
 #ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32
@@ -64,7 +58,7 @@ struct SceneParams {
     float h_lo_scale, h_hi_scale;  // 10/thickness, 2.5/thickness, per 2^-16 m
     float sun[3], sun_rad[3], ambient[3];
     float hg_g, hg_norm, absorption, light_step, tau_max;  // hg_norm = (1 - g^2)/(4 pi)
-    float k0, b_cut, inv_1mc, detail_w, rho0;
+    float k0, inv_1mc, detail_w, rho0;
     int log2_base, log2_detail, log2_weather;
     int light_steps, integration, constant_mode;
     // detail coordinates = (base + half_base) << detail_shift - half_detail when
@@ -194,16 +188,9 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
     if (g <= 0.0f) return 0.0f;
     float cb[8], cd[8], cw[4];
     load_rec8(base, rec3(lb, c[kBX], c[kBY], c[kBZ]), cb);
-#if !CLOUDVOL_DETAIL_AFTER_BASE
     if (FX || detail) load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
-#endif
     if (FX || weather) load_rec4(weather, rec2(lw, c[kWX], c[kWY]), cw);
     const float b = trilerp(cb, lb, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
-#if CLOUDVOL_DETAIL_AFTER_BASE
-    // B <= c: the (non-negative) detail term cannot make the density positive
-    if (b + p.b_cut <= 0.0f) return 0.0f;
-    if (FX || detail) load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
-#endif
     float r = b + p.k0;
     if (FX || detail) {
         const float dt = trilerp(cd, ld, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();

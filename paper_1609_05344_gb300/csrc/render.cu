@@ -74,7 +74,6 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
     const double wd = vol->log2_detail ? d.detail_weight : 0.0;
     p->detail_w = (float)wd;
     p->k0 = (float)(0.5 - d.coverage - 0.5 * wd);
-    p->b_cut = (float)(0.5 - d.coverage);
     p->inv_1mc = (float)(1.0 / (1.0 - d.coverage));
     p->rho0 = (float)d.constant_density;
     p->log2_base = vol->log2_base;
