@@ -249,8 +249,11 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "fast-1080p", "width": wl.width, "height": wl.height,
-                       "steps": wl.steps, "light_steps": wl.light_steps, "jitter": True,
-                       "taa": True, "volumes": "128^3 base + 32^3 detail + 512^2 weather"},
+                       "steps": wl.steps, "light_steps": wl.light_steps, "jitter": "pixel",
+                       "taa": True, "blend": 0.1, "volume_precision": "fp64 (the oracle's own)",
+                       "volumes": "128^3 base + 32^3 detail + 512^2 weather",
+                       "sample": "the raymarch dominates the oracle's frame; motion and the "
+                                 "resolve are not in the band sample"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"render of one {wl.width}x{band} band per step, FP64, "
                                        f"{cores} threads, scaled to a frame"},
