@@ -326,6 +326,12 @@ int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const 
 int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width, int cloud_height,
                     const float *background, float *out, int width, int height, void *stream);
 
+/* Number of bounded device-side waits that gave up since the last reset (a
+ * bulk copy into shared memory that did not complete; the affected tile's
+ * outputs are left unwritten instead of waiting without limit).  Zero in
+ * normal operation.  Synchronous; reset != 0 clears the counter. */
+int cloud_device_wait_timeouts(unsigned int *count, int reset);
+
 /* ---- sessions: one camera's stream of TAA frames ------------------------- */
 
 /* A session owns the device buffers of one view (current frame, two history

@@ -148,6 +148,7 @@ SIGNATURES = [
     ("taa_resolve", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _vp]),
     ("cloud_taa_reproject", _i, [_vp, _P(Params), _P(Camera), _P(Camera), _vp, _vp, _vp, _i, _i, _i,
                                  ctypes.c_float, _vp]),
+    ("cloud_device_wait_timeouts", _i, [_P(ctypes.c_uint), _i]),
     ("cloud_composite", _i, [_vp, _i, _i, _i, _vp, _vp, _i, _i, _vp]),
     ("cloud_session_create", _i, [_vp, _i, _i, _i, _P(_vp)]),
     ("cloud_session_destroy", _i, [_vp]),

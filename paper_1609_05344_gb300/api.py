@@ -281,6 +281,14 @@ def hash4(keys: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
+def device_wait_timeouts(reset: bool = False) -> int:
+    """Bounded device waits that gave up (cloud_device_wait_timeouts); 0 normally."""
+    n = ctypes.c_uint()
+    N.check(N.lib().cloud_device_wait_timeouts(ctypes.byref(n), int(reset)),
+            "cloud_device_wait_timeouts")
+    return n.value
+
+
 def launch_config(precision: str, light_steps: int) -> int:
     """The launch configuration renders of this precision and light-step count
     use (cloud_get_launch_config)."""

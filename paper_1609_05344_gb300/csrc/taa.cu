@@ -6,6 +6,11 @@
 // neighbourhood reads of the current frame and the 2x2 history footprint are
 // served by L1; each pixel's own current value, motion and output are the
 // compulsory traffic.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cloudvol {
@@ -208,42 +213,71 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
 // Reprojection and TAA resolve fused (Sec. 3.2): each pixel's motion is
 // computed in registers (the motion kernel's arithmetic, bitwise) instead
 // of being written and read back; the current frame's 3x3 neighbourhoods come
-// from a shared-memory tile with a clamped one-pixel halo, copied with
-// cp.async while the motion is computed; each thread resolves two vertically
-// adjacent pixels, whose 3x3 windows share two rows.
+// from a shared-memory tile with a clamped one-pixel halo, brought in by one
+// TMA bulk tensor copy while the motion is computed; each thread resolves two
+// vertically adjacent pixels, whose 3x3 windows share two rows.
 constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
 #ifndef CLOUDVOL_TAA_MIN_BLOCKS
 #define CLOUDVOL_TAA_MIN_BLOCKS 3  // CTAs per SM the fused kernel is compiled for (74 registers)
 #endif
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem) : "memory");
+// Waits that gave up (a bulk copy that never completed): counted on the
+// device, read by cloud_device_wait_timeouts.  Every wait below is bounded.
+__device__ unsigned int g_wait_timeouts = 0;
+constexpr int kWaitPolls = 1 << 16;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(const uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    for (int it = 0; it < kWaitPolls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 template <typename H>
-__global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_kernel(const __grid_constant__ MotionParams mp,
+__global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_kernel(const __grid_constant__ CUtensorMap tile_map,
+                                                            const __grid_constant__ MotionParams mp,
                                                             const H *__restrict__ hist,
-                                                            const float4 *__restrict__ cur,
                                                             H *__restrict__ out, float blend) {
-    __shared__ __align__(16) float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(8) uint64_t bar;
     const int W = mp.width, Hh = mp.height;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = x0 + tx;
-    // 1. current-frame tile with a clamped one-pixel halo, copied to shared
-    //    memory asynchronously while the motion is computed: warp row ty copies
-    //    tile rows ty, ty + 8, ty + 16; lanes 0 and 1 also the two right columns
-    {
-        const int gx = min(max(x - 1, 0), W - 1), gx2 = min(x + 31, W - 1);
-#pragma unroll
-        for (int r = ty; r < kTH + 2; r += 8) {
-            const float4 *row = cur + (size_t)min(max(y0 + r - 1, 0), Hh - 1) * W;
-            cp_async16(&tile[r][tx], row + gx);
-            if (tx < 2) cp_async16(&tile[r][kTW + tx], row + gx2);
-        }
+    const int tid = ty * 32 + tx;
+    // 1. current-frame tile with a one-pixel halo (34 x 18 texels), one TMA
+    //    bulk copy issued by one thread, landing while the motion is computed.
+    //    The box starts at texel (x0 - 1, y0 - 1): its x offset in bytes is
+    //    16 (x0 - 1), a multiple of 16; texels outside the frame arrive as
+    //    zeros and are replaced by their clamped neighbours below.
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        constexpr unsigned kTileBytes = (kTH + 2) * (kTW + 2) * 16;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                     ::"r"(smem_addr(&bar)), "r"(kTileBytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];\n"
+            ::"r"(smem_addr(&tile[0][0])), "l"(&tile_map), "r"(4 * (x0 - 1)), "r"(y0 - 1),
+              "r"(smem_addr(&bar))
+            : "memory");
+    }
     // 2. motion (registers only) and the history footprint of both pixels
     //    (rows 2 ty and 2 ty + 1 of the tile): column terms once, the two
     //    pixels' arithmetic interleaved, the rare FP64 near-tie calls after
@@ -283,8 +317,29 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_ke
             use[r] = true;
         }
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+    const bool landed = mbar_wait(&bar, 0);
+    if (!__syncthreads_and(landed)) {
+        // the copy did not complete within the bounded wait: count it, give the
+        // copy one more bounded wait so that it cannot land after the CTA exits,
+        // and leave the outputs of this tile unwritten
+        if (tid == 0) {
+            atomicAdd(&g_wait_timeouts, 1u);
+            mbar_wait(&bar, 0);
+        }
+        return;
+    }
+    // texels outside the frame: clamp to the edge (border tiles only); every
+    // source is an in-frame texel of the tile and every target an outside one
+    const int r_lo = max(0, 1 - y0), r_hi = min(kTH + 1, Hh - y0);
+    const int c_lo = max(0, 1 - x0), c_hi = min(kTW + 1, W - x0);
+    if (r_lo > 0 || c_lo > 0 || r_hi < kTH + 1 || c_hi < kTW + 1) {
+        for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
+            const int r = i / (kTW + 2), c = i - r * (kTW + 2);
+            const int rr = min(max(r, r_lo), r_hi), cc = min(max(c, c_lo), c_hi);
+            if (rr != r || cc != c) tile[r][c] = tile[rr][cc];
+        }
+        __syncthreads();
+    }
     if (x >= W) return;
     // 3. 3x3 ranges of both pixels from four tile rows (row-wise min/max, then
     //    the two overlapping row triples share their middle pair), clamp the
@@ -413,6 +468,33 @@ int launch_taa(const void *history, const float *current, const float *motion, v
     return check_launch("taa_kernel");
 }
 
+// Tensor map of the current frame for the resolve's tile copy: the frame as
+// a 2-D FP32 array of 4 W x H elements (row stride 16 W bytes), box 4 (kTW + 2)
+// x (kTH + 2) elements, zero fill outside.  The encoder is the driver's,
+// fetched through the runtime once.
+static int current_tile_map(const float *current, int width, int height, CUtensorMap *map) {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return set_error(CLOUD_ERR_CUDA, "cloud_taa_reproject: cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[2] = {4ull * (cuuint64_t)width, (cuuint64_t)height};
+    const cuuint64_t strides[1] = {16ull * (cuuint64_t)width};
+    const cuuint32_t box[2] = {4u * (kTW + 2), (cuuint32_t)(kTH + 2)};
+    const cuuint32_t elem[2] = {1u, 1u};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(current), dims,
+                              strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(CLOUD_ERR_CUDA, "cloud_taa_reproject: tensor map rejected");
+    return CLOUD_OK;
+}
+
 int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                          const cloud_camera *cur, const void *history, const float *current,
                          void *history_out, int width, int height, int fmt, float blend,
@@ -433,14 +515,14 @@ int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const
         if (a < b + px * eb && b < a + px * eb)
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: history and history_out overlap");
     }
+    CUtensorMap map;
+    if (int rc = current_tile_map(current, width, height, &map)) return rc;
     const dim3 grid((width + kTW - 1) / kTW, (height + kTH - 1) / kTH), block(32, 8);
     if (fmt == CLOUD_HISTORY_FP32)
-        taa_reproject_kernel<float4><<<grid, block, 0, s>>>(p, (const float4 *)history,
-                                                            (const float4 *)current,
+        taa_reproject_kernel<float4><<<grid, block, 0, s>>>(map, p, (const float4 *)history,
                                                             (float4 *)history_out, blend);
     else
-        taa_reproject_kernel<uint2><<<grid, block, 0, s>>>(p, (const uint2 *)history,
-                                                           (const float4 *)current,
+        taa_reproject_kernel<uint2><<<grid, block, 0, s>>>(map, p, (const uint2 *)history,
                                                            (uint2 *)history_out, blend);
     return check_launch("taa_reproject_kernel");
 }
@@ -535,4 +617,18 @@ extern "C" int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width
     clear_error();
     return launch_composite(cloud, cloud_fmt, cloud_width, cloud_height, background, out, width,
                             height, (cudaStream_t)stream);
+}
+
+extern "C" int cloud_device_wait_timeouts(unsigned int *count, int reset) {
+    clear_error();
+    if (!count) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_device_wait_timeouts: null pointer");
+    if (int rc = check_cuda(cudaMemcpyFromSymbol(count, g_wait_timeouts, sizeof(unsigned int)),
+                            "cloud_device_wait_timeouts"))
+        return rc;
+    if (reset) {
+        const unsigned int zero = 0;
+        return check_cuda(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(unsigned int)),
+                          "cloud_device_wait_timeouts");
+    }
+    return CLOUD_OK;
 }

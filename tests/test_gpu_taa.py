@@ -192,3 +192,11 @@ def test_session_frame_device_view_and_buffer_checks(api):
                    out=torch.empty((48, 63, 4), device="cuda"))
     with pytest.raises(ValueError):
         api.taa(None, torch.empty((48, 64, 4), device="cuda"), torch.empty((48, 64, 1), device="cuda"))
+
+
+def test_zz_no_device_wait_gave_up(api):
+    """Every bounded wait of the resolve kernels in this module's tests completed
+    (the tile copies all landed)."""
+    import torch
+    torch.cuda.synchronize()
+    assert api.device_wait_timeouts() == 0
