@@ -745,6 +745,91 @@ def run_paper_table(args):
     return 0
 
 
+def run_config_table(args):
+    """The three single-view configurations (plain tiny, 720p reference quality,
+    1080p fast path with FP32 and FP16 tiles) on GB300 beside the FP64 oracle
+    timed on one host thread and on all host cores (the oracle on 16 evenly
+    spaced rows, scaled to a frame), with the max-abs RGBA error of the GPU
+    render against the oracle on those rows."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_1609_05344_gb300 import _native, api, inputs as I
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    _native.build()
+    cores = os.cpu_count() or 1
+    flush = L2Flush()
+    stream = torch.cuda.current_stream()
+    prm = I.params()
+    rows = []
+    cases = [("plain-tiny", "fp32"), ("reference", "fp32"), ("fast-1080p", "fp32"),
+             ("fast-1080p", "fp16")]
+    for name, prec in cases:
+        wl = I.workload(name, precision=prec)
+        W, H, S, LS = wl.width, wl.height, wl.steps, wl.light_steps
+        vol = api.Volume(wl.volume)
+        cam = (lambda f: I.orbit_camera(f, wl.volume["seed"])) if wl.taa else (
+            lambda f: I.ground_camera())
+        jit = (lambda f: f) if wl.jitter else (lambda f: -1)
+        cur = torch.empty((H, W, 4), device="cuda")
+        hist = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+
+        def frame(f):
+            api.render(vol, cam(f), prm, W, H, S, LS, jitter_frame=jit(f), out=cur)
+            if wl.taa:
+                api.taa_reproject(vol, prm, cam(f - 1) if f else None, cam(f),
+                                  hist[(f + 1) % 2] if f else None, cur, out=hist[f % 2])
+        for f in range(args.warmup):
+            frame(f)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush(k)
+            evs[k][0].record(stream)
+            frame(args.warmup + k)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        gpu_ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+        # oracle rows (FP64 tiles regardless of the GPU's storage precision)
+        ys = np.unique(np.linspace(0, H - 1, min(16, H)).astype(np.int32))
+        xs_all = np.tile(np.arange(W, dtype=np.int32), ys.size)
+        ys_all = np.repeat(ys, W)
+        ovol = O.Volume(dict(wl.volume, precision="fp32"))
+        f0 = 0
+        t = {}
+        for nt in (1, cores):
+            t0 = time.perf_counter()
+            ref, _ = O.render_pixels(ovol, cam(f0), prm, W, H, S, LS, xs_all, ys_all,
+                                     jitter_frame=jit(f0), nthreads=nt)
+            t[nt] = (time.perf_counter() - t0) * H / ys.size
+        gpu = api.render(vol, cam(f0), prm, W, H, S, LS, jitter_frame=jit(f0)).cpu().numpy()
+        err = float(np.abs(gpu[ys_all, xs_all].astype(np.float64) - ref).max())
+        ovol.close()
+        vol.close()
+        samples = W * H * S * (1 + LS)
+        rows.append({"config": name, "volume_precision": prec, "size": f"{W}x{H}",
+                     "steps": S, "light_steps": LS, "jitter": wl.jitter, "taa": wl.taa,
+                     "gpu_ms_per_frame": gpu_ms,
+                     "gpu_nominal_gsamples_s": samples / (gpu_ms * 1e-3) / 1e9,
+                     "oracle_1_thread_ms_per_frame": t[1] * 1e3,
+                     "oracle_all_cores_ms_per_frame": t[cores] * 1e3, "cores": cores,
+                     "oracle_sample": f"render of {ys.size} evenly spaced rows, scaled to a frame",
+                     "max_abs_err_vs_fp64_on_those_rows": err})
+    fast = next(r for r in rows if r["config"] == "fast-1080p" and r["volume_precision"] == "fp32")
+    line = {"metric": "ms/frame per configuration on GB300 beside the FP64 oracle",
+            "value": fast["gpu_ms_per_frame"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fast["gpu_ms_per_frame"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "config-table",
+                       "l2": "flushed between frames (256 MiB write + 256 MiB read, untimed)"},
+            "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -757,7 +842,7 @@ def main(argv=None):
                     help="fast-1080p start offsets: per pixel (Sec. 3.2), one per frame "
                          "(Sec. 4), or none (midpoint samples)")
     ap.add_argument("--workload", default="fast-1080p",
-                    choices=["fast-1080p", "batched-64", "served", "paper-table"])
+                    choices=["fast-1080p", "batched-64", "served", "paper-table", "config-table"])
     args = ap.parse_args(argv)
     args.precision_set = any(a.startswith("--precision") for a in (argv or sys.argv[1:]))
     if args.warmup < 3:
@@ -766,6 +851,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batched-64":
         return run_batched(args)
+    if args.workload == "config-table":
+        return run_config_table(args)
     if args.workload == "served":
         return run_served(args)
     if args.workload == "paper-table":
