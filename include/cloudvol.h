@@ -311,7 +311,10 @@ int taa_resolve(const void *history, const float *current, const float *motion,
 /* cloud_motion followed by taa_resolve, fused into one kernel: the motion of
  * each pixel (camera `prev` -> `cur`, exactly as cloud_motion computes it) is
  * used in registers and never stored.  history == NULL is a first frame (prev
- * may then be NULL).  Buffers as in taa_resolve. */
+ * may then be NULL).  Buffers as in taa_resolve; `current` is read through a
+ * TMA tensor map built for this call (width*height contiguous float4), so it
+ * must stay valid until the launch completes.  Results are bitwise those of
+ * cloud_motion + taa_resolve. */
 int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                         const cloud_camera *cur, const void *history, const float *current,
                         void *history_out, int width, int height, int history_fmt, float blend,
