@@ -131,3 +131,50 @@ def test_failed_request_is_reported_not_hung(api):
     with pytest.raises(CloudError):
         srv.submit(sid, _orbit(0, 2), 8)
     srv.close()
+
+
+def test_concurrent_submitters(api):
+    """Four host threads drive their own sessions at once (the binding releases
+    the interpreter lock inside each call): every session's frames are bitwise
+    the frames of the same session served alone."""
+    import threading
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    w, h, frames = 48, 32, 4
+    alone = {k: _run_alone_orbit(api, vol, w, h, frames, k) for k in range(4)}
+    srv = api.Server(vol, I.params(), history_fmt="fp32", max_batch_views=16, slots=2)
+    sids = {k: srv.open_session(w, h) for k in range(4)}
+    got, errors = {}, []
+
+    def drive(k):
+        try:
+            outs = []
+            for f in range(frames):
+                srv.wait(srv.submit(sids[k], _orbit(k, f), 8))
+                outs.append(srv.output(sids[k]))
+            got[k] = outs
+        except Exception as exc:  # reported below, never swallowed
+            errors.append(exc)
+
+    threads = [threading.Thread(target=drive, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=60)
+    st = srv.stats()
+    srv.close()
+    assert not errors and all(not t.is_alive() for t in threads)
+    assert st["completed"] == 4 * frames
+    for k in range(4):
+        for a, m in zip(alone[k], got[k]):
+            assert np.array_equal(a, m)
+
+
+def _run_alone_orbit(api, vol, w, h, frames, k):
+    srv = api.Server(vol, I.params(), history_fmt="fp32", max_batch_views=8)
+    sid = srv.open_session(w, h)
+    outs = []
+    for f in range(frames):
+        srv.wait(srv.submit(sid, _orbit(k, f), 8))
+        outs.append(srv.output(sid))
+    srv.close()
+    return outs
