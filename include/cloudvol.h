@@ -164,7 +164,8 @@ typedef struct {
     uint64_t session_bytes;
 } cloud_server_counters;
 
-/* ---- status ------------------------------------------------------------ */
+/* ---- status ------------------------------------------------------------  * Library plumbing; no counterpart in the paper.
+ */
 const char *cloud_status_string(int status);
 /* Last failure on the calling thread ("" if none). */
 const char *cloud_last_error_message(void);
@@ -178,13 +179,15 @@ const char *cloud_last_error_message(void);
  * `stream` has passed the generation work.  *out is set only on success. */
 int cloud_volume_create(const cloud_volume_desc *desc, void *stream, cloud_volume **out);
 
-/* Frees a volume.  The caller guarantees that no enqueued work still uses it. */
+/* Frees a volume.  The caller guarantees that no enqueued work still uses it.  * (Volume lifetime; the tiles are those of cloud_volume_create, Sec. 1.)
+ */
 int cloud_volume_destroy(cloud_volume *vol);
 
 /* Copies the noise tiles into caller-owned device buffers as float values
  * in [0, 1) (decoding reduced-precision storage): base base_n^3, detail
  * detail_n^3, weather weather_n^2, x fastest.  Any pointer may be NULL to
- * skip that tile.  For tests and tools. */
+ * skip that tile.  For tests and tools.  * (The density tiles of Sec. 1, decoded for checks.)
+ */
 int cloud_volume_export(const cloud_volume *vol, float *base, float *detail, float *weather,
                         void *stream);
 
@@ -211,7 +214,9 @@ int cloud_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
 
 /* As cloud_render, and also adds the number of density evaluations the
  * launch performed to *lookups (device, one uint64, caller-owned; the caller
- * zeroes it).  Measures the effective work of a frame. */
+ * zeroes it).  Measures the effective work of a frame.  * (The lookups are the density samples of Sec. 1: one per view step
+ * plus one per light step of each step with density.)
+ */
 int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
                        int width, int height, int steps, int light_steps, int jitter_frame,
                        int integration, float *out_rgba, unsigned long long *lookups,
@@ -233,7 +238,9 @@ int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const c
  * new servers use for volumes of `precision` rendered with `light_steps`
  * light steps (e.g. to restore a configuration an earlier autotune found).
  * config outside [0, CLOUD_TUNE_CONFIGS) or a bad precision is
- * CLOUD_ERR_INVALID_ARG.  Process-wide; host only. */
+ * CLOUD_ERR_INVALID_ARG.  Process-wide; host only.  * Scheduling only; no counterpart in the paper (the pixel results do not
+ * depend on it).
+ */
 int cloud_get_launch_config(int precision, int light_steps, int *config);
 int cloud_set_launch_config(int precision, int light_steps, int config);
 
@@ -249,7 +256,9 @@ int cloud_autotune_render(const cloud_volume *vol, const cloud_camera *cam, cons
  * the views' pixel tiles form a work queue (longest step counts first) that
  * resident CTAs drain through a device counter.  The library allocates and
  * owns the view table and the counter.  Each view's output equals a
- * cloud_render of that view. */
+ * cloud_render of that view.  * (Each view is the raymarch of Sec. 1 / Sec. 3.1 / Sec. 3.2 exactly as
+ * cloud_render; batching itself has no counterpart in the paper.)
+ */
 int cloud_batch_create(const cloud_volume *vol, const cloud_params *prm, int light_steps,
                        int integration, const cloud_view *views, int n_views, cloud_batch **out);
 int cloud_batch_destroy(cloud_batch *b);
@@ -291,7 +300,8 @@ int cloud_batch_render_static(const cloud_volume *vol, const cloud_params *prm, 
  * each pixel of camera `cur` relative to camera `prev`: the pixel's ray
  * entry point into the cloud layer (or the point at t_max for rays that do
  * not enter it ahead of the camera) is projected into `prev`;
- * motion = pixel centre - that projection.  Points behind `prev` get 1e9. */
+ * motion = pixel centre - that projection.  Points behind `prev` get 1e9.  * (The per-pixel reprojection the TAA of Sec. 3.2 needs.)
+ */
 int cloud_motion(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                  const cloud_camera *cur, int width, int height, float *motion, void *stream);
 
@@ -314,7 +324,8 @@ int taa_resolve(const void *history, const float *current, const float *motion,
  * may then be NULL).  Buffers as in taa_resolve; `current` is read through a
  * TMA tensor map built for this call (width*height contiguous float4), so it
  * must stay valid until the launch completes.  Results are bitwise those of
- * cloud_motion + taa_resolve. */
+ * cloud_motion + taa_resolve.  * (Sec. 3.2: reprojection and the TAA resolve.)
+ */
 int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                         const cloud_camera *cur, const void *history, const float *current,
                         void *history_out, int width, int height, int history_fmt, float blend,
@@ -332,7 +343,8 @@ int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width, int cloud
 /* Number of bounded device-side waits that gave up since the last reset (a
  * bulk copy into shared memory that did not complete; the affected tile's
  * outputs are left unwritten instead of waiting without limit).  Zero in
- * normal operation.  Synchronous; reset != 0 clears the counter. */
+ * normal operation.  Synchronous; reset != 0 clears the counter.  * Failure reporting; no counterpart in the paper.
+ */
 int cloud_device_wait_timeouts(unsigned int *count, int reset);
 
 /* ---- sessions: one camera's stream of TAA frames ------------------------- */
@@ -344,10 +356,10 @@ int cloud_session_create(const cloud_volume *vol, int width, int height, int his
                          cloud_session **out);
 int cloud_session_destroy(cloud_session *s);
 
-/* One frame: render with jitter_frame = the session's frame index, then the
- * fused reprojection (motion from the previous frame's camera) and TAA
- * resolve into the other history buffer (cloud_taa_reproject), advance the
- * index.  If host_out is not NULL the resolved frame
+/* One frame of Sec. 3.2: render with jitter_frame = the session's frame
+ * index, then the fused reprojection (motion from the previous frame's
+ * camera) and TAA resolve into the other history buffer
+ * (cloud_taa_reproject), advance the index.  If host_out is not NULL the resolved frame
  * (width*height*4 values of the history format) is copied to it and the
  * call waits for the stream; otherwise it returns after enqueueing.
  * *dev_out (if not NULL) receives the device address of the resolved frame,
@@ -417,7 +429,8 @@ int cloud_server_stats(cloud_server *srv, cloud_server_counters *st);
 
 /* out[i] = hash(keys[4i], keys[4i+1], keys[4i+2], keys[4i+3]) on the device
  * (the counter-based hash of the jitter and the noise lattice).  keys and
- * out are device buffers of 4n and n uint32. */
+ * out are device buffers of 4n and n uint32.  * (The counter-based hash behind the Sec. 3.2 offsets and the noise lattice.)
+ */
 int cloud_hash4_batch(const uint32_t *keys, int64_t n, uint32_t *out, void *stream);
 
 #ifdef __cplusplus
