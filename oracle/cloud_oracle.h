@@ -84,13 +84,16 @@ typedef struct {
     int jitter_mode;        /* ORC_JITTER_PER_PIXEL or ORC_JITTER_PER_FRAME      */
 } orc_params;
 
-/* Counter-based hash (PCG output permutation over one LCG step). */
+/* Counter-based hash (PCG output permutation over one LCG step; Jarzynski and
+ * Olano, JCGT 2020): the generator behind the Sec. 3.2 start offsets and the
+ * noise lattice. */
 uint32_t orc_pcg(uint32_t v);
 uint32_t orc_hash4(uint32_t a, uint32_t b, uint32_t c, uint32_t d);
 double orc_unit(uint32_t h); /* (h >> 8) * 2^-24, in [0,1) */
 void orc_hash4_batch(const uint32_t *keys /* n x 4 */, long n, uint32_t *out);
 
-/* Noise volumes. */
+/* Noise volumes: the density field Sec. 1 samples at every step ([reading]:
+ * value-noise fBm tiles, coverage remap, weather map, height profile). */
 int orc_volume_build(const orc_volume_desc *desc, orc_volume *vol);
 void orc_volume_free(orc_volume *vol);
 double orc_fbm3(uint32_t seed, uint32_t salt, int n, int kx, int ky, int kz);
@@ -98,17 +101,20 @@ double orc_fbm2(uint32_t seed, uint32_t salt, int n, int kx, int ky);
 double orc_height_gradient(const orc_volume_desc *d, double z);
 double orc_density(const orc_volume *vol, const double p[3]);
 
-/* Scattering. */
+/* Scattering: the Henyey-Greenstein phase function Sec. 1 names. */
 double orc_hg(double mu, double g);
 
-/* Geometry. */
+/* Geometry: one pinhole ray per pixel and the cloud layer it crosses
+ * (Sec. 1); the per-pixel / per-frame start offset (Sec. 3.2, Sec. 4). */
 void orc_pixel_ray(const orc_camera *cam, int width, int height, int x, int y, double d[3]);
 int orc_slab_clip(const orc_volume_desc *d, const orc_params *prm, const double o[3],
                   const double dir[3], double *t0, double *t1);
 double orc_jitter(uint32_t seed, int x, int y, int frame);
 
-/* Raymarch of one pixel; out = premultiplied RGBA; *lookups counts density
- * evaluations.  jitter_frame < 0 puts every sample at the middle of its step. */
+/* Raymarch of one pixel (Sec. 1 march and light march, Sec. 3.1 per-step
+ * integral, Sec. 3.2 start offset); out = premultiplied RGBA; *lookups counts
+ * density evaluations.  jitter_frame < 0 puts every sample at the middle of
+ * its step. */
 void orc_render_pixel(const orc_volume *vol, const orc_camera *cam, const orc_params *prm,
                       int width, int height, int x, int y, int steps, int light_steps,
                       int jitter_frame, int integration, double out[4], long long *lookups);
@@ -125,20 +131,21 @@ long long orc_render_pixels(const orc_volume *vol, const orc_camera *cam,
                             const int *xs, const int *ys, int n, int nthreads, double *out);
 
 /* Screen-space motion of each pixel from the previous camera to the current
- * one, in pixels: m = current pixel centre - its reprojection in prev. */
+ * one, in pixels (the reprojection the TAA of Sec. 3.2 needs): m = current
+ * pixel centre - its reprojection in prev. */
 void orc_motion_pixel(const orc_volume_desc *d, const orc_params *prm, const orc_camera *prev,
                       const orc_camera *cur, int width, int height, int x, int y, double m[2]);
 void orc_motion(const orc_volume_desc *d, const orc_params *prm, const orc_camera *prev,
                 const orc_camera *cur, int width, int height, double *motion);
 
-/* TAA resolve of one pixel.  history may be NULL (first frame). */
+/* TAA resolve of one pixel (Sec. 3.2).  history may be NULL (first frame). */
 void orc_taa_pixel(const double *history, const double *current, const double *motion,
                    int width, int height, int x, int y, double blend, int clamp, double out[4]);
 void orc_taa(const double *history, const double *current, const double *motion, int width,
              int height, double blend, int clamp, double *out);
 
-/* Composite (Sec. 3.2: the TAA-resolved low-resolution cloud buffer is
- * composited into the scene).  cloud: sw x sh premultiplied RGBA; bg and out:
+/* Composite (Sec. 3.2: the resolved low-resolution buffer goes into the
+ * scene; [reading] bilinear resample and premultiplied "over").  cloud: sw x sh premultiplied RGBA; bg and out:
  * dw x dh RGBA.  out = C + (1 - C.a) bg with C the bilinear sample of cloud at
  * ((x + 1/2) sw/dw - 1/2, (y + 1/2) sh/dh - 1/2), clamp to edge. */
 void orc_composite(const double *cloud, int sw, int sh, const double *bg, int dw, int dh,
