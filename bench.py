@@ -114,14 +114,14 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def march_code_sha1():
-    """SHA-1 (12 hex digits) of the march sources with comments and blank lines
-    removed: it changes when the code does, not when a comment does."""
+def _code_sha1(files):
+    """SHA-1 (12 hex digits) of sources with comments and blank lines removed:
+    it changes when the code does, not when a comment does."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_1609_05344_gb300", "csrc")
     h = hashlib.sha1()
-    for f in ("march.cuh", "march_kernels.cuh", "render.cu", "common.cuh"):
+    for f in files:
         with open(os.path.join(csrc, f)) as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         for line in text.splitlines():
@@ -129,6 +129,32 @@ def march_code_sha1():
             if line:
                 h.update(line.encode() + b"\n")
     return h.hexdigest()[:12]
+
+
+def march_code_sha1():
+    """Comment-insensitive SHA-1 of the march sources."""
+    return _code_sha1(("march.cuh", "march_kernels.cuh", "render.cu", "common.cuh"))
+
+
+def taa_code_sha1():
+    """Comment-insensitive SHA-1 (12 hex digits) of the resolve's source."""
+    return _code_sha1(("taa.cu", "common.cuh"))
+
+
+def taa_profile():
+    """DRAM bytes per launch of the fused resolve from the committed ncu summary,
+    or {} when its code has changed since."""
+    prof = os.path.join(ROOT, "profiles", "taa_motion_kernels_fast-1080p.md")
+    if not os.path.exists(prof):
+        return {}
+    vals = {}
+    for line in open(prof):
+        if ":" in line and line.split(":")[0] in ("code_sha1", "traffic_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            vals[k] = v.strip()
+    if vals.get("code_sha1") != taa_code_sha1():
+        return {}
+    return {"traffic": int(vals["traffic_bytes_per_launch"])}
 
 
 def march_profile():
@@ -451,6 +477,7 @@ def run_gpu(args):
                      "frac_of_sector_rate": achieved / sector_peak_gbs},
         "taa_roofline": {"bound": "hbm", "achieved": taa_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": taa_gbs / pk["hbm_gbs"], "bytes_per_pixel": taa_bytes_px,
+                         "traffic": taa_profile().get("traffic"),
                          "kernel": "taa_reproject_kernel",
                          "peak_source": pk["source"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_s * 1e3, "frames": n_e2e,
