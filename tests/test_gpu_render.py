@@ -181,7 +181,9 @@ def test_telescoping_no_sun_on_gpu(api):
 
 
 @pytest.mark.parametrize("case", ["inside-layer", "looking-down", "no-light-steps", "one-step",
-                                  "no-early-out", "horizontal", "above-layer", "above-looking-up"])
+                                  "no-early-out", "horizontal", "above-layer", "above-looking-up",
+                                  "on-bottom", "on-top-looking-down", "far-clip",
+                                  "horizontal-below"])
 def test_edge_cases(api, oracle, case):
     desc = I.volume_desc("full", seed=5)
     vol, ovol = api.Volume(desc), oracle.Volume(desc)
@@ -204,6 +206,14 @@ def test_edge_cases(api, oracle, case):
         cam = I.camera((300.0, -200.0, 6000.0), 70.0, -25.0, 70.0)
     elif case == "above-looking-up":  # every ray misses (quick test from above)
         cam = I.camera((300.0, -200.0, 6000.0), 70.0, 30.0, 40.0)
+    elif case == "on-bottom":  # camera exactly on the layer bottom
+        cam = I.camera((50.0, 80.0, 1500.0), 15.0, 20.0, 60.0)
+    elif case == "on-top-looking-down":  # exactly on the top, looking into the layer
+        cam = I.camera((50.0, 80.0, 4000.0), 200.0, -30.0, 60.0)
+    elif case == "far-clip":  # shallow rays: t_max = 40 km ends most marches
+        cam = I.camera((0.0, 0.0, 0.0), 30.0, 3.0, 10.0)
+    elif case == "horizontal-below":  # the middle row is exactly horizontal and misses
+        cam = I.camera((0.0, 0.0, 500.0), 10.0, 0.0, 50.0)
     w, h = 33, 17
     got = api.render(vol, cam, prm, w, h, steps, ls, jitter_frame=1).cpu().numpy()
     ref, _ = oracle.render(ovol, cam, prm, w, h, steps, ls, jitter_frame=1, nthreads=8)
@@ -212,6 +222,8 @@ def test_edge_cases(api, oracle, case):
         assert np.all(got == 0.0)
     if case == "above-layer":
         assert ref[..., 3].max() > 0.5 and (ref[..., 3] == 0).any()
+    if case == "horizontal-below":
+        assert np.all(got[h // 2] == 0.0)
 
 
 def test_lookup_count_matches_oracle(api, oracle):

@@ -200,3 +200,31 @@ def test_zz_no_device_wait_gave_up(api):
     import torch
     torch.cuda.synchronize()
     assert api.device_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("jump", ["yaw-40", "behind", "translate-2km", "above-layer"])
+def test_fused_resolve_large_camera_jumps(api, oracle, jump):
+    """Camera jumps that push much of the history off screen or behind the
+    previous camera: the fused kernel against the oracle's motion + resolve on
+    the same current frame and history."""
+    rng = np.random.default_rng(11)
+    desc = I.volume_desc("full", seed=3)
+    vol = api.Volume(desc)
+    prm = I.params()
+    w, h = 97, 61
+    cur_cam = I.camera((0.0, 0.0, 500.0), 30.0, 15.0, 60.0)
+    prev_cam = {
+        "yaw-40": I.camera((0.0, 0.0, 500.0), 70.0, 15.0, 60.0),
+        "behind": I.camera((0.0, 0.0, 500.0), 210.0, 15.0, 60.0),
+        "translate-2km": I.camera((1500.0, -1300.0, 500.0), 30.0, 15.0, 60.0),
+        "above-layer": I.camera((0.0, 0.0, 5000.0), 30.0, -20.0, 60.0),
+    }[jump]
+    hist = I.synthetic_frame(rng, h, w)
+    cur = I.synthetic_frame(rng, h, w)
+    got = api.taa_reproject(vol, prm, prev_cam, cur_cam, _t(hist), _t(cur), blend=0.1).cpu().numpy()
+    omot = oracle.motion(desc, prm, prev_cam, cur_cam, w, h)
+    ref = oracle.taa(hist.astype(np.float64), cur.astype(np.float64), omot, blend=0.1)
+    off = (omot[..., 0] > np.arange(w)[None, :] + 0.5) | (omot[..., 0] < np.arange(w)[None, :] + 0.5 - w) | \
+          (omot[..., 1] > np.arange(h)[:, None] + 0.5) | (omot[..., 1] < np.arange(h)[:, None] + 0.5 - h)
+    assert off.any()  # the jump really sends pixels off screen
+    assert np.abs(got.astype(np.float64) - ref).max() <= 1e-4
