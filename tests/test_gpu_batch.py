@@ -125,3 +125,30 @@ def test_every_launch_config_bitwise_equal(api, precision):
                 assert np.array_equal(a, o), N.config_parts(cfg)
     finally:
         api.set_launch_config(precision, 6, keep)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 1e-1)])
+def test_batched_64_full_size_sampled(api, oracle, precision, tol):
+    """The batched workload at its full size (64 seeded views, 256x256 .. 1920x1080,
+    8 / 16 / 32 / 128 steps) in the launch the bench times (one persistent launch
+    from a CUDA graph), checked on sampled pixels of every view against the FP64
+    oracle: FP32 tiles at the 1e-4 bar, BF16 tiles against their stated-error
+    guard."""
+    desc = I.volume_desc("full", seed=3, precision=precision)
+    vol, ovol = api.Volume(desc), oracle.Volume(dict(desc, precision="fp32"))
+    views = I.random_views(64, seed=4)
+    b = api.Batch(vol, I.params(), views)
+    outs = b.render(graph=True)
+    rng = np.random.default_rng(9)
+    worst = 0.0
+    for v, o in zip(views, outs):
+        xs = rng.integers(0, v["width"], 24)
+        ys = rng.integers(0, v["height"], 24)
+        got = o.cpu().numpy()[ys, xs]
+        ref, _ = oracle.render_pixels(ovol, v["camera"], I.params(), v["width"], v["height"],
+                                      v["steps"], 6, xs, ys, jitter_frame=v["jitter_frame"],
+                                      nthreads=8)
+        worst = max(worst, float(np.abs(got - ref).max()))
+    b.close()
+    print(f"batched-64 {precision}: max abs err {worst:.3e} on 1536 sampled pixels")
+    assert worst <= tol
