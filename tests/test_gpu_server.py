@@ -178,3 +178,32 @@ def _run_alone_orbit(api, vol, w, h, frames, k):
         outs.append(srv.output(sid))
     srv.close()
     return outs
+
+
+def test_served_full_size_fp16(api, oracle):
+    """The served configuration at its largest session (1920x1080, FP16 tiles
+    and FP16 history) next to a small one in the same batches: three frames of
+    each against the FP64 oracle chain (render -> motion -> TAA), within the
+    FP16 stated-error guard; the small session is also bitwise the same alone."""
+    desc = I.volume_desc("full", seed=3, precision="fp16")
+    vol, ovol = api.Volume(desc), oracle.Volume(dict(desc, precision="fp32"))
+    prm = I.params()
+    sizes = [(1920, 1080), (640, 360)]
+    srv = api.Server(vol, prm, history_fmt="fp16", max_batch_views=8, slots=2)
+    sids = [srv.open_session(w, h) for w, h in sizes]
+    ohist = [None, None]
+    worst = 0.0
+    for f in range(3):
+        tickets = [srv.submit(sid, _orbit(k, f), 8) for k, sid in enumerate(sids)]
+        for t in tickets:
+            srv.wait(t)
+        for k, (w, h) in enumerate(sizes):
+            cam = _orbit(k, f)
+            ocur, _ = oracle.render(ovol, cam, prm, w, h, 8, 6, jitter_frame=f, nthreads=16)
+            omot = (oracle.motion(desc, prm, _orbit(k, f - 1), cam, w, h) if f
+                    else np.zeros((h, w, 2)))
+            ohist[k] = oracle.taa(ohist[k], ocur, omot, blend=0.1)
+            worst = max(worst, float(np.abs(srv.output(sids[k]).astype(np.float64) - ohist[k]).max()))
+    srv.close()
+    print(f"served fp16 full size: max abs err {worst:.3e}")
+    assert worst <= 5e-2
