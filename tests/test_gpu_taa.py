@@ -228,3 +228,34 @@ def test_fused_resolve_large_camera_jumps(api, oracle, jump):
           (omot[..., 1] > np.arange(h)[:, None] + 0.5) | (omot[..., 1] < np.arange(h)[:, None] + 0.5 - h)
     assert off.any()  # the jump really sends pixels off screen
     assert np.abs(got.astype(np.float64) - ref).max() <= 1e-4
+
+
+def test_fast_1080p_full_orbit_chain(api, oracle):
+    """The benchmarked configuration end to end: 1920x1080, 8 jittered x 6 light
+    steps, FP32 tiles, render + fused reprojection + TAA over the whole 32-frame
+    orbit, every resolved frame against the FP64 oracle chain at 1e-4."""
+    import time
+    import torch
+    wl = I.workload("fast-1080p")
+    desc = wl.volume
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    prm = I.params()
+    W, H = wl.width, wl.height
+    sess = api.Session(vol, W, H, history_fmt="fp32")
+    host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+    ohist, worst, t0 = None, 0.0, time.perf_counter()
+    seed = desc["seed"]
+    for f in range(wl.frames):
+        cam = I.orbit_camera(f, seed)
+        sess.frame(cam, prm, wl.steps, wl.light_steps, blend=0.1, host_out=host)
+        ocur, _ = oracle.render(ovol, cam, prm, W, H, wl.steps, wl.light_steps, jitter_frame=f,
+                                nthreads=16)
+        omot = (oracle.motion(desc, prm, I.orbit_camera(f - 1, seed), cam, W, H) if f
+                else np.zeros((H, W, 2)))
+        ohist = oracle.taa(ohist, ocur, omot, blend=0.1)
+        err = float(np.abs(host.numpy().astype(np.float64) - ohist).max())
+        worst = max(worst, err)
+        assert err <= 1e-4, (f, err)
+    sess.close()
+    print(f"fast-1080p orbit chain: worst max abs err {worst:.3e} over {wl.frames} frames "
+          f"({time.perf_counter() - t0:.0f} s)")
