@@ -141,6 +141,21 @@ def test_reference_720p_sampled(api, oracle):
     assert err <= TOL_FP32
 
 
+@pytest.mark.parametrize("integration", ["analytic", "basic"])
+def test_reference_720p_full_image(api, oracle, integration):
+    """The reference-quality configuration (1280x720, 128 x 6 steps, full tiles,
+    no jitter) on every pixel, for both integration rules."""
+    wl = I.workload("reference")
+    vol, ovol = api.Volume(wl.volume), oracle.Volume(wl.volume)
+    cam, prm = I.ground_camera(), I.params()
+    got = api.render(vol, cam, prm, wl.width, wl.height, wl.steps, wl.light_steps,
+                     integration=integration).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, prm, wl.width, wl.height, wl.steps, wl.light_steps,
+                           integration=oracle.ANALYTIC if integration == "analytic" else oracle.BASIC,
+                           nthreads=16)
+    assert _max_err(got, ref) <= TOL_FP32
+
+
 def _closed_form(oracle, desc, prm, cam, w, h, rho0, ls):
     out = np.zeros((h, w, 4))
     s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
