@@ -10,6 +10,9 @@ and the integration rules of Sec. 3.1.
 * Beer-Lambert (Sec. 1): alpha = 1 - exp(-alpha D sum_i rho_i), independent
   of the lighting.
 * Convergence: analytic and basic rules approach the same limit as N grows.
+* By hand: one and two (jittered) view steps of a pixel written out from the
+  method's formulas, sharing only the separately pinned density and hash with
+  the oracle, pin the light-march placement and sum and the step chaining.
 """
 import math
 
@@ -202,3 +205,85 @@ def test_per_frame_jitter_shares_one_offset(oracle):
         assert img[y, x, 3] == pytest.approx(-math.expm1(-prm["absorption"] * D * rho), abs=1e-13)
     pix, _ = oracle.render(vol, cam, I.params(tau_max=0.0), w, h, n, 6, jitter_frame=5)
     assert not np.allclose(pix, img)  # per-pixel jitter differs
+
+
+@pytest.mark.parametrize("light_steps", [1, 6, 32])
+def test_one_step_pixel_by_hand(oracle, light_steps):
+    """One view step of one pixel, written out from Sec. 1 / Sec. 3.1 with the
+    oracle's (separately pinned) density as the only shared piece: the view
+    sample at the middle of the layer segment, light samples at
+    p + (j + 1/2) dl s towards the sun (zero density above the layer), tau_sun =
+    alpha dl sum rho_j, L_in = E e^{-tau_sun} p_HG(d.s) + A, and the analytic
+    step C = L_in (1 - e^{-alpha rho D}).  Pins the light-march placement,
+    direction and sum, which a constant-density slab cannot see."""
+    desc = I.volume_desc("full", seed=7)
+    vol = oracle.Volume(desc)
+    prm = I.params()
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    checked = above = 0
+    for yaw in range(0, 360, 5):
+        for pitch in (8.0, 20.0, 45.0):
+            cam = I.camera((0.0, 0.0, 500.0), float(yaw), pitch, 60.0)
+            d = oracle.pixel_ray(cam, 1, 1, 0, 0)
+            o = np.array(cam["pos"])
+            hit, t0, t1 = oracle.slab_clip(desc, prm, o, d)
+            if not hit:
+                continue
+            D = t1 - t0
+            p = o + (t0 + 0.5 * D) * d
+            rho = vol.density(p)
+            if rho <= 0.0:
+                continue
+            qs = [p + (j + 0.5) * prm["light_step"] * s for j in range(light_steps)]
+            above += sum(q[2] > desc["slab_hi"] for q in qs)
+            tau_sun = prm["absorption"] * prm["light_step"] * sum(vol.density(q) for q in qs)
+            lin = (np.array(prm["sun_radiance"]) * math.exp(-tau_sun) *
+                   oracle.hg(float(np.dot(d, s)), prm["hg_g"]) + np.array(prm["ambient"]))
+            a = -math.expm1(-prm["absorption"] * rho * D)
+            want = np.concatenate([lin * a, [a]])
+            got, _ = oracle.render(vol, cam, prm, 1, 1, 1, light_steps, nthreads=1)
+            assert np.allclose(got[0, 0], want, rtol=1e-12, atol=1e-14), (yaw, pitch)
+            checked += 1
+    assert checked >= 10
+    if light_steps == 32:
+        assert above > 0  # some light samples left the layer (density 0 there)
+
+
+def test_two_jittered_steps_by_hand(oracle):
+    """Two view steps with the Sec. 3.2 offset, by hand: samples at
+    t0 + (i + u) D with u the pixel's jitter value, each step's light from its
+    own light march, and the second step attenuated by the first's optical
+    depth (C = L_1 (1 - e^{-s_1}) + e^{-s_1} L_2 (1 - e^{-s_2}), s_i = alpha rho_i D)."""
+    desc = I.volume_desc("full", seed=7)
+    vol = oracle.Volume(desc)
+    prm = I.params()
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    al, dl = prm["absorption"], prm["light_step"]
+    checked = 0
+    for yaw in range(0, 360, 7):
+        cam = I.camera((0.0, 0.0, 500.0), float(yaw), 12.0, 60.0)
+        w = h = 3
+        x, y, frame = 2, 1, 5
+        d = oracle.pixel_ray(cam, w, h, x, y)
+        o = np.array(cam["pos"])
+        hit, t0, t1 = oracle.slab_clip(desc, prm, o, d)
+        if not hit:
+            continue
+        u = oracle.jitter(desc["seed"], x, y, frame)
+        D = (t1 - t0) / 2
+        ph = oracle.hg(float(np.dot(d, s)), prm["hg_g"])
+        c, tau = np.zeros(3), 0.0
+        for i in range(2):
+            p = o + (t0 + (i + u) * D) * d
+            rho = vol.density(p)
+            if rho <= 0.0:
+                continue
+            tsun = al * dl * sum(vol.density(p + (j + 0.5) * dl * s) for j in range(6))
+            lin = np.array(prm["sun_radiance"]) * math.exp(-tsun) * ph + np.array(prm["ambient"])
+            c += math.exp(-tau) * lin * -math.expm1(-al * rho * D)
+            tau += al * rho * D
+        want = np.concatenate([c, [-math.expm1(-tau)]])
+        got, _ = oracle.render(vol, cam, prm, w, h, 2, 6, jitter_frame=frame, nthreads=1)
+        assert np.allclose(got[y, x], want, rtol=1e-12, atol=1e-14), yaw
+        checked += tau > 0
+    assert checked >= 5
