@@ -223,6 +223,22 @@ __device__ __forceinline__ void load_rec4(const T *tile, uint32_t rec, float c[4
     c[2] = d.x; c[3] = d.y;
 }
 
+// Host side of the multi-view resolve (taa.cu), used by the render server:
+// one request per view (prev == NULL and history == NULL for a first frame).
+struct ResolveRequest {
+    const cloud_camera *prev, *cur;
+    const void *history;
+    const float *current;
+    void *out;
+    int width, height;
+};
+// Builds the per-view table in h_table (pinned host, resolve_view_bytes() per
+// view), uploads it to d_table on s and launches one kernel over all views.
+int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
+                               const ResolveRequest *reqs, int n, int fmt, float blend,
+                               void *h_table, void *d_table, cudaStream_t s);
+size_t resolve_view_bytes();
+
 // Plain (unpacked) texel loads, decoded to the centred value.
 __device__ __forceinline__ float load_texel(const float *p, uint32_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_texel(const __half *p, uint32_t i) {

@@ -7,8 +7,8 @@
 // one request per session (a session's next frame needs the history its
 // previous frame produces) and at most max_batch_views requests, in arrival
 // order.  The batch's raymarch is one persistent launch over all its views,
-// followed by each request's fused motion + TAA resolve, all on the slot's
-// stream; a host callback at the end of the stream work stamps the completion
+// followed by one launch resolving every request (fused motion + TAA), all on
+// the slot's stream; a host callback at the end of the stream work stamps the completion
 // time.  With two or more slots, a batch formed while another is on the GPU
 // overlaps with it.  Sessions keep their history, raw frame and jitter index
 // on the device; opening one is admitted only while the free
@@ -33,10 +33,6 @@ namespace cloudvol {
 int launch_batch(const cloud_volume *vol, const SceneParams &scene, const ViewParams *d_views,
                  int n_views, int total_tiles, int config, unsigned int *d_work,
                  unsigned long long *counter, cudaStream_t s);
-int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
-                         const cloud_camera *cur, const void *history, const float *current,
-                         void *history_out, int width, int height, int fmt, float blend,
-                         cudaStream_t s);
 }  // namespace cloudvol
 
 using namespace cloudvol;
@@ -76,9 +72,12 @@ struct Slot {
     cudaStream_t stream = nullptr;
     ViewParams *h_table = nullptr;  // pinned
     ViewParams *d_table = nullptr;
+    void *h_rtable = nullptr;       // pinned: the resolve's per-view table
+    void *d_rtable = nullptr;
     unsigned int *d_work = nullptr;
     bool busy = false;
     std::vector<uint64_t> reqs;
+    std::vector<ResolveRequest> resolves;
 };
 
 }  // namespace
@@ -164,18 +163,25 @@ int launch_slot(cloud_server *srv, int si, const std::vector<Request *> &batch) 
     if (int rc = launch_batch(srv->vol, srv->scene, sl.d_table, n, next, srv->config, sl.d_work,
                               nullptr, sl.stream))
         return rc;
+    // every request's reprojection motion and TAA resolve in one launch (the
+    // motion is never stored)
+    sl.resolves.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const Request &r = *batch[i];
+        const Session &se = srv->sessions[r.session];
+        sl.resolves[i] = ResolveRequest{se.has_history ? &se.prev_cam : nullptr, &r.cam,
+                                        se.has_history ? se.hist[se.latest] : nullptr, se.current,
+                                        se.hist[1 - se.latest], se.width, se.height};
+    }
+    if (int rc = launch_taa_reproject_batch(srv->vol, &srv->prm, sl.resolves.data(), n,
+                                            srv->cfg.history_fmt, srv->cfg.blend, sl.h_rtable,
+                                            sl.d_rtable, sl.stream))
+        return rc;
     for (const Request *rp : batch) {
+        // the session stays busy until this slot completes, so its state can advance now
         const Request &r = *rp;
         Session &se = srv->sessions[r.session];
-        const int nxt = 1 - se.latest;
-        // reprojection motion and TAA resolve fused (the motion is never stored)
-        const int rc = launch_taa_reproject(srv->vol, &srv->prm, se.has_history ? &se.prev_cam : nullptr,
-                                            &r.cam, se.has_history ? se.hist[se.latest] : nullptr,
-                                            se.current, se.hist[nxt], se.width, se.height,
-                                            srv->cfg.history_fmt, srv->cfg.blend, sl.stream);
-        if (rc) return rc;
-        // the session stays busy until this slot completes, so its state can advance now
-        se.latest = nxt;
+        se.latest = 1 - se.latest;
         se.has_history = true;
         se.prev_cam = r.cam;
         se.frame += 1;
@@ -292,6 +298,12 @@ extern "C" int cloud_server_create(const cloud_volume *vol, const cloud_params *
             rc = check_cuda(cudaMalloc(&sl.d_table, sizeof(ViewParams) * cfg->max_batch_views),
                             "cudaMalloc view table");
         if (!rc) rc = check_cuda(cudaMalloc(&sl.d_work, sizeof(unsigned int)), "cudaMalloc counter");
+        if (!rc)
+            rc = check_cuda(cudaMallocHost(&sl.h_rtable, resolve_view_bytes() * cfg->max_batch_views),
+                            "cudaMallocHost resolve table");
+        if (!rc)
+            rc = check_cuda(cudaMalloc(&sl.d_rtable, resolve_view_bytes() * cfg->max_batch_views),
+                            "cudaMalloc resolve table");
     }
     if (!rc) {
         try {
@@ -306,6 +318,8 @@ extern "C" int cloud_server_create(const cloud_volume *vol, const cloud_params *
             if (sl.h_table) cudaFreeHost(sl.h_table);
             if (sl.d_table) cudaFree(sl.d_table);
             if (sl.d_work) cudaFree(sl.d_work);
+            if (sl.h_rtable) cudaFreeHost(sl.h_rtable);
+            if (sl.d_rtable) cudaFree(sl.d_rtable);
         }
         delete srv;
         return rc;
@@ -329,6 +343,8 @@ extern "C" int cloud_server_destroy(cloud_server *srv) {
         cudaFreeHost(sl.h_table);
         cudaFree(sl.d_table);
         cudaFree(sl.d_work);
+        cudaFreeHost(sl.h_rtable);
+        cudaFree(sl.d_rtable);
     }
     for (auto &se : srv->sessions)
         if (se.open) free_session_buffers(se);

@@ -245,15 +245,17 @@ __device__ __forceinline__ bool mbar_wait(const uint64_t *bar, unsigned parity) 
     return false;
 }
 
+// One 32x16-pixel tile (bx, by) of the fused resolve: the body of both the
+// single-view kernel and the multi-view kernel.  tile_map points to the
+// current frame's tensor map (kernel parameter or global memory), tile and bar
+// are the block's shared memory.
 template <typename H>
-__global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_kernel(const __grid_constant__ CUtensorMap tile_map,
-                                                            const __grid_constant__ MotionParams mp,
-                                                            const H *__restrict__ hist,
-                                                            H *__restrict__ out, float blend) {
-    __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
-    __shared__ __align__(8) uint64_t bar;
+__device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const MotionParams &mp,
+                                             const H *__restrict__ hist, H *__restrict__ out,
+                                             float blend, int bx, int by,
+                                             float4 (&tile)[kTH + 2][kTW + 2], uint64_t &bar) {
     const int W = mp.width, Hh = mp.height;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    const int x0 = bx * kTW, y0 = by * kTH;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = x0 + tx;
     const int tid = ty * 32 + tx;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_ke
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3}], [%4];\n"
-            ::"r"(smem_addr(&tile[0][0])), "l"(&tile_map), "r"(4 * (x0 - 1)), "r"(y0 - 1),
+            ::"r"(smem_addr(&tile[0][0])), "l"(tile_map), "r"(4 * (x0 - 1)), "r"(y0 - 1),
               "r"(smem_addr(&bar))
             : "memory");
     }
@@ -367,6 +369,57 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS) taa_reproject_ke
         }
         store_hist(out, (size_t)y * W + x, res);
     }
+}
+
+template <typename H>
+__global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
+    taa_reproject_kernel(const __grid_constant__ CUtensorMap tile_map,
+                         const __grid_constant__ MotionParams mp, const H *__restrict__ hist,
+                         H *__restrict__ out, float blend) {
+    __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(8) uint64_t bar;
+    resolve_tile<H>(&tile_map, mp, hist, out, blend, blockIdx.x, blockIdx.y, tile, bar);
+}
+
+// Many views' resolves in one launch (the render server's batches): block b
+// is tile b of the concatenated views' tile lists; its view is found by
+// binary search over the views' first tiles and its motion constants staged
+// in shared memory.  Each tile is computed exactly as by taa_reproject_kernel.
+struct alignas(64) ResolveView {
+    CUtensorMap map;  // the view's current frame
+    MotionParams mp;
+    const void *hist;
+    void *out;
+    float blend;
+    int tiles_x, tile_begin;
+};
+
+template <typename H>
+__global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
+    taa_reproject_batch_kernel(const ResolveView *__restrict__ views, int n_views) {
+    __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ MotionParams smp;
+    __shared__ int s_view;
+    const int t = blockIdx.x, tid = threadIdx.y * 32 + threadIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = n_views - 1;  // last view with tile_begin <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (views[mid].tile_begin <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        s_view = lo;
+    }
+    __syncthreads();
+    const ResolveView &rv = views[s_view];
+    const int *src = reinterpret_cast<const int *>(&rv.mp);
+    int *dst = reinterpret_cast<int *>(&smp);
+    for (int i = tid; i < (int)(sizeof(MotionParams) / 4); i += 256) dst[i] = src[i];
+    __syncthreads();
+    const int local = t - rv.tile_begin;
+    resolve_tile<H>(&rv.map, smp, (const H *)rv.hist, (H *)rv.out, rv.blend, local % rv.tiles_x,
+                    local / rv.tiles_x, tile, bar);
 }
 
 int build_motion_params(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
@@ -526,6 +579,56 @@ int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const
                                                            (uint2 *)history_out, blend);
     return check_launch("taa_reproject_kernel");
 }
+
+int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
+                               const ResolveRequest *reqs, int n, int fmt, float blend,
+                               void *h_table_v, void *d_table_v, cudaStream_t s) {
+    if (!vol || !prm || !reqs || n < 1 || !h_table_v || !d_table_v)
+        return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: bad arguments");
+    if (fmt != CLOUD_HISTORY_FP32 && fmt != CLOUD_HISTORY_FP16)
+        return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: bad history format");
+    if (!(blend >= 0.0f && blend <= 1.0f))
+        return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: blend outside [0, 1]");
+    ResolveView *h_table = static_cast<ResolveView *>(h_table_v);
+    int next = 0;
+    const size_t eb = fmt == CLOUD_HISTORY_FP32 ? 16 : 8;
+    for (int i = 0; i < n; ++i) {
+        const ResolveRequest &r = reqs[i];
+        if (!r.cur || !r.current || !r.out || (r.history && !r.prev))
+            return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: null pointer");
+        ResolveView &v = h_table[i];
+        if (int rc = build_motion_params(vol, prm, r.history ? r.prev : r.cur, r.cur, r.width,
+                                         r.height, &v.mp))
+            return rc;
+        const size_t px = (size_t)r.width * r.height;
+        if (!aligned(r.current, 16) || !aligned(r.out, eb) || (r.history && !aligned(r.history, eb)))
+            return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: misaligned buffer");
+        if (r.history) {
+            const char *a = (const char *)r.history, *b = (const char *)r.out;
+            if (a < b + px * eb && b < a + px * eb)
+                return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: history and output overlap");
+        }
+        if (int rc = current_tile_map(r.current, r.width, r.height, &v.map)) return rc;
+        v.hist = r.history;
+        v.out = r.out;
+        v.blend = blend;
+        v.tiles_x = (r.width + kTW - 1) / kTW;
+        v.tile_begin = next;
+        next += v.tiles_x * ((r.height + kTH - 1) / kTH);
+    }
+    if (int rc = check_cuda(cudaMemcpyAsync(d_table_v, h_table, sizeof(ResolveView) * n,
+                                            cudaMemcpyHostToDevice, s),
+                            "resolve batch: upload table"))
+        return rc;
+    const ResolveView *d_table = static_cast<const ResolveView *>(d_table_v);
+    if (fmt == CLOUD_HISTORY_FP32)
+        taa_reproject_batch_kernel<float4><<<next, dim3(32, 8), 0, s>>>(d_table, n);
+    else
+        taa_reproject_batch_kernel<uint2><<<next, dim3(32, 8), 0, s>>>(d_table, n);
+    return check_launch("taa_reproject_batch_kernel");
+}
+
+size_t resolve_view_bytes() { return sizeof(ResolveView); }
 
 // Composite (Sec. 3.2): the low-resolution cloud buffer, resampled
 // bilinearly to the display size, laid over the background (premultiplied

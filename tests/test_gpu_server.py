@@ -207,3 +207,26 @@ def test_served_full_size_fp16(api, oracle):
     srv.close()
     print(f"served fp16 full size: max abs err {worst:.3e}")
     assert worst <= 5e-2
+
+
+def test_served_frames_equal_session_frames(api):
+    """The server's batched raymarch and batched resolve compute each frame
+    exactly as a session does with its single-view launches (bitwise)."""
+    import torch
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    prm = I.params()
+    w, h, frames = 72, 40, 4
+    sess = api.Session(vol, w, h, "fp32")
+    host = torch.empty((h, w, 4), dtype=torch.float32, pin_memory=True)
+    srv = api.Server(vol, prm, history_fmt="fp32", max_batch_views=8)
+    sid = srv.open_session(w, h)
+    other = srv.open_session(50, 30)  # a second view in the same batches
+    for f in range(frames):
+        sess.frame(_orbit(0, f), prm, 8, 6, host_out=host)
+        t = srv.submit(sid, _orbit(0, f), 8)
+        t2 = srv.submit(other, _orbit(1, f), 16)
+        srv.wait(t)
+        srv.wait(t2)
+        assert np.array_equal(srv.output(sid), host.numpy()), f
+    srv.close()
+    sess.close()
