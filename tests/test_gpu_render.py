@@ -301,3 +301,31 @@ def test_maximum_sizes(api, oracle):
     deep = api.render(vol, cam, I.params(tau_max=0.0), 6, 4, 4096, 6).cpu().numpy()
     ref, _ = oracle.render(ovol, cam, I.params(tau_max=0.0), 6, 4, 4096, 6, nthreads=8)
     assert _max_err(deep, ref) <= TOL_FP32
+
+
+def test_random_cameras_and_settings(api, oracle):
+    """Seeded random cameras (inside, below and above the layer, any yaw, pitch
+    from -70 to 80 degrees, fov 15-100), step counts, light steps, offsets and
+    integration rules on small ragged images, against the oracle at 1e-4."""
+    rng = np.random.default_rng(2024)
+    desc = I.volume_desc("full", seed=9)
+    vol, ovol = api.Volume(desc), oracle.Volume(desc)
+    worst = 0.0
+    for _ in range(24):
+        cam = I.camera((float(rng.uniform(-5000, 5000)), float(rng.uniform(-5000, 5000)),
+                        float(rng.choice([rng.uniform(0, 1400), rng.uniform(1600, 3900),
+                                          rng.uniform(4100, 7000)]))),
+                       float(rng.uniform(0, 360)), float(rng.uniform(-70, 80)),
+                       float(rng.uniform(15, 100)))
+        w, h = int(rng.integers(1, 24)), int(rng.integers(1, 16))
+        steps, ls = int(rng.integers(1, 25)), int(rng.integers(0, 9))
+        frame = int(rng.integers(-1, 50))
+        integ = str(rng.choice(["analytic", "basic"]))
+        prm = I.params(jitter_mode=str(rng.choice(["pixel", "frame"])))
+        got = api.render(vol, cam, prm, w, h, steps, ls, jitter_frame=frame,
+                         integration=integ).cpu().numpy()
+        ref, _ = oracle.render(ovol, cam, prm, w, h, steps, ls, jitter_frame=frame,
+                               integration=oracle.ANALYTIC if integ == "analytic" else oracle.BASIC,
+                               nthreads=8)
+        worst = max(worst, _max_err(got, ref))
+    assert worst <= TOL_FP32
