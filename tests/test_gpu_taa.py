@@ -259,3 +259,32 @@ def test_fast_1080p_full_orbit_chain(api, oracle):
     sess.close()
     print(f"fast-1080p orbit chain: worst max abs err {worst:.3e} over {wl.frames} frames "
           f"({time.perf_counter() - t0:.0f} s)")
+
+
+def test_fused_resolve_random_camera_pairs(api, oracle):
+    """Seeded random (previous, current) camera pairs, sizes and blends: the fused
+    reprojection + resolve against the oracle's motion + resolve on the same
+    current frame and history, FP32 history at 1e-4."""
+    rng = np.random.default_rng(77)
+    desc = I.volume_desc("full", seed=3)
+    vol = api.Volume(desc)
+    prm = I.params()
+    worst = 0.0
+    for _ in range(16):
+        def cam():
+            return I.camera((float(rng.uniform(-3000, 3000)), float(rng.uniform(-3000, 3000)),
+                             float(rng.uniform(0, 6000))), float(rng.uniform(0, 360)),
+                            float(rng.uniform(-50, 70)), float(rng.uniform(30, 90)))
+        cur_cam = cam()
+        prev_cam = cam() if rng.uniform() < 0.5 else dict(
+            cur_cam, pos=tuple(np.array(cur_cam["pos"]) + rng.normal(0, 30, 3)))
+        w, h = int(rng.integers(1, 90)), int(rng.integers(1, 60))
+        blend = float(rng.uniform(0.02, 0.5))
+        hist = I.synthetic_frame(rng, h, w)
+        cur = I.synthetic_frame(rng, h, w)
+        got = api.taa_reproject(vol, prm, prev_cam, cur_cam, _t(hist), _t(cur),
+                                blend=blend).cpu().numpy()
+        omot = oracle.motion(desc, prm, prev_cam, cur_cam, w, h)
+        ref = oracle.taa(hist.astype(np.float64), cur.astype(np.float64), omot, blend=blend)
+        worst = max(worst, float(np.abs(got.astype(np.float64) - ref).max()))
+    assert worst <= 1e-4
