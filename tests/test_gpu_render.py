@@ -185,6 +185,37 @@ def test_homogeneous_slab_closed_form_on_gpu(api, oracle, steps):
     assert _max_err(got, _closed_form(oracle, desc, prm, cam, w, h, rho0, 6)) <= 2e-5
 
 
+@pytest.mark.parametrize("steps", [1, 2, 3, 8])
+def test_basic_rule_homogeneous_closed_form_on_gpu(api, oracle, steps):
+    """Basic rule (Sec. 3.1) in a homogeneous slab: the transmittance advanced
+    over a step weights that step's light, RGB = L_in sigma D sum_{i=1..N}
+    e^{-i sigma D}, summed as a geometric series."""
+    rho0 = 0.004
+    desc = I.volume_desc("constant", rho0=rho0)
+    prm = I.params(tau_max=0.0)
+    cam = I.ground_camera()
+    w, h = 40, 24
+    got = api.render(api.Volume(desc), cam, prm, w, h, steps, 6, jitter_frame=2,
+                     integration="basic").cpu().numpy()
+    exp = np.zeros((h, w, 4))
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    sigma = rho0 * prm["absorption"]
+    for y in range(h):
+        for x in range(w):
+            d = oracle.pixel_ray(cam, w, h, x, y)
+            hit, t0, t1 = oracle.slab_clip(desc, prm, cam["pos"], d)
+            if not hit:
+                continue
+            ph = oracle.hg(float(np.dot(d, s)), prm["hg_g"])
+            lin = (np.array(prm["sun_radiance"]) * math.exp(-sigma * 6 * prm["light_step"]) * ph
+                   + np.array(prm["ambient"]))
+            sd = sigma * (t1 - t0) / steps
+            geo = math.exp(-sd) * -math.expm1(-steps * sd) / -math.expm1(-sd)
+            exp[y, x, :3], exp[y, x, 3] = lin * sd * geo, -math.expm1(-sigma * (t1 - t0))
+    assert exp[..., 3].max() > 0.3
+    assert _max_err(got, exp) <= 2e-5
+
+
 def test_telescoping_no_sun_on_gpu(api):
     desc = I.volume_desc("full", seed=3)
     prm = I.params(sun_radiance=(0.0, 0.0, 0.0))

@@ -6,6 +6,9 @@ and the integration rules of Sec. 3.1.
   RGB = L_in (1 - e^{-rho0 alpha (t1 - t0)}) for EVERY step count and jitter
   (the step-length independence claimed in Sec. 3.1 / Fig. 2); the basic rule
   S = T L does not, and converges to it as the step shrinks.
+* Basic rule, homogeneous slab: the transmittance advanced over a step weights
+  that step's light, so RGB = L_in sigma D sum_{i=1..N} e^{-i sigma D} (a
+  geometric series, summed in closed form).
 * Telescoping: with no sun, RGB = A * alpha exactly for any density field.
 * Beer-Lambert (Sec. 1): alpha = 1 - exp(-alpha D sum_i rho_i), independent
   of the lighting.
@@ -102,6 +105,46 @@ def test_homogeneous_slab_closed_form(oracle, steps, jitter_frame):
             assert np.allclose(img[y, x], exp, atol=1e-12, rtol=0), (x, y)
             hits += exp[3] > 0
     assert hits > w * h // 3
+
+
+def _basic_closed_form_pixel(oracle, desc, prm, cam, w, h, x, y, rho0, light_steps, n):
+    """Basic rule (Sec. 3.1: the transmittance is advanced over a step before it
+    weights that step's light) in a homogeneous slab, summed in closed form: with
+    q = e^{-sigma D}, RGB = L_in sigma D (q + q^2 + ... + q^N)
+    = L_in sigma D q (1 - q^N) / (1 - q); alpha = 1 - q^N.  Weighting by the
+    transmittance before the step instead would drop one factor q."""
+    d = oracle.pixel_ray(cam, w, h, x, y)
+    hit, t0, t1 = oracle.slab_clip(desc, prm, cam["pos"], d)
+    if not hit:
+        return np.zeros(4)
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    tau_sun = rho0 * prm["absorption"] * light_steps * prm["light_step"]
+    ph = oracle.hg(float(np.dot(d, s)), prm["hg_g"])
+    l_in = np.array(prm["sun_radiance"]) * math.exp(-tau_sun) * ph + np.array(prm["ambient"])
+    sd = rho0 * prm["absorption"] * (t1 - t0) / n
+    q = math.exp(-sd)
+    geo = q * -math.expm1(-n * sd) / -math.expm1(-sd)
+    return np.concatenate([l_in * sd * geo, [-math.expm1(-rho0 * prm["absorption"] * (t1 - t0))]])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 8])
+@pytest.mark.parametrize("jitter_frame", [-1, 4])
+def test_basic_rule_homogeneous_closed_form(oracle, steps, jitter_frame):
+    rho0 = 0.004
+    desc = I.volume_desc("constant", rho0=rho0)
+    prm = I.params(tau_max=0.0)
+    vol = oracle.Volume(desc)
+    cam = I.ground_camera()
+    w, h = 24, 16
+    img, _ = oracle.render(vol, cam, prm, w, h, steps, 6, jitter_frame=jitter_frame,
+                           integration=oracle.BASIC)
+    hits = 0
+    for y in range(h):
+        for x in range(w):
+            exp = _basic_closed_form_pixel(oracle, desc, prm, cam, w, h, x, y, rho0, 6, steps)
+            assert np.allclose(img[y, x], exp, atol=1e-12, rtol=0), (x, y)
+            hits += exp[3] > 0.3
+    assert hits > w * h // 4
 
 
 def test_basic_rule_depends_on_step_length(oracle):
