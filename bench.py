@@ -141,40 +141,30 @@ def taa_code_sha1():
     return _code_sha1(("taa.cu", "common.cuh"))
 
 
+def _profile_data(name, code_hash):
+    """Counters from the data file committed beside an ncu summary
+    (profiles/<name>.json), or {} when the kernel code has changed since they
+    were taken."""
+    path = os.path.join(ROOT, "profiles", name + ".json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        d = json.load(f)
+    return d if d.get("code_sha1") == code_hash else {}
+
+
 def taa_profile():
-    """DRAM bytes per launch of the fused resolve from the committed ncu summary,
-    or {} when its code has changed since."""
-    prof = os.path.join(ROOT, "profiles", "taa_motion_kernels_fast-1080p.md")
-    if not os.path.exists(prof):
-        return {}
-    vals = {}
-    for line in open(prof):
-        if ":" in line and line.split(":")[0] in ("code_sha1", "traffic_bytes_per_launch"):
-            k, v = line.split(":", 1)
-            vals[k] = v.strip()
-    if vals.get("code_sha1") != taa_code_sha1():
-        return {}
-    return {"traffic": int(vals["traffic_bytes_per_launch"])}
+    """DRAM bytes per launch of the fused resolve from the committed ncu capture."""
+    d = _profile_data("taa_motion_kernels_fast-1080p", taa_code_sha1())
+    return {"traffic": d["traffic_bytes_per_launch"]} if d else {}
 
 
 def march_profile():
-    """Counters of the march from the committed ncu summary (DRAM bytes per
-    launch, ncu's L1TEX throughput in % of peak), or {} when the kernel code has
-    changed since they were taken."""
-    h = march_code_sha1()
-    prof = os.path.join(ROOT, "profiles", "march_kernel_fast-1080p.md")
-    if not os.path.exists(prof):
-        return {}
-    keys = ("code_sha1", "traffic_bytes_per_launch", "l1tex_throughput_pct")
-    vals = {}
-    for line in open(prof):
-        if ":" in line and line.split(":")[0] in keys:
-            k, v = line.split(":", 1)
-            vals[k] = v.strip()
-    if vals.get("code_sha1") != h:
-        return {}
-    return {"traffic": int(vals["traffic_bytes_per_launch"]),
-            "l1tex_pct": float(vals["l1tex_throughput_pct"])}
+    """Counters of the march from the committed ncu capture (DRAM bytes per
+    launch, ncu's L1TEX throughput in % of peak)."""
+    d = _profile_data("march_kernel_fast-1080p", march_code_sha1())
+    return ({"traffic": d["traffic_bytes_per_launch"], "l1tex_pct": d["l1tex_throughput_pct"]}
+            if d else {})
 
 
 def dist_env():
@@ -433,9 +423,10 @@ def run_gpu(args):
     pk = _peaks()
     mprof = march_profile()
     sm_mhz = pk["sm_max_mhz"]
-    l1_peak_gbs = 152 * L1TEX_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    l1_peak_gbs = sms * L1TEX_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9
     # scattered 32-byte records: at most one L1 data-pipe wavefront (sector) per clock per SM
-    sector_peak_gbs = 152 * 32 * sm_mhz * 1e6 / 1e9
+    sector_peak_gbs = sms * 32 * sm_mhz * 1e6 / 1e9
     texel_b = 4 if args.precision == "fp32" else 2  # bytes per stored texel
     bytes_per_lookup = 20 * texel_b  # 8 base + 8 detail + 4 weather texels
     march_avg = statistics.mean(march_ms)
@@ -470,7 +461,7 @@ def run_gpu(args):
                      "frac": achieved / l1_peak_gbs, "traffic": mprof.get("traffic"),
                      "ncu_l1tex_throughput_pct_of_peak": mprof.get("l1tex_pct"),
                      "kernel": "march_kernel",
-                     "peak_source": f"L1TEX data path 152 SMs x 128 B/clk x {sm_mhz:.0f} MHz "
+                     "peak_source": f"L1TEX data path {sms} SMs x 128 B/clk x {sm_mhz:.0f} MHz "
                                     f"({pk['source']} clock)",
                      "algorithmic_bytes_per_lookup": bytes_per_lookup,
                      "sector_rate_peak": sector_peak_gbs,
@@ -488,6 +479,7 @@ def run_gpu(args):
                       "application runs them (wall clock over all frames incl. pipeline "
                       "fill and drain)"},
         "gpu_launches": launches,
+        "device_wait_timeouts": api.device_wait_timeouts(),
         "clocks": dict(clk.summary(), window="warm-up and timed frames"),
     }
     if world == 1 and not args.no_cpu_baseline:

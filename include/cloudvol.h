@@ -164,8 +164,9 @@ typedef struct {
     uint64_t session_bytes;
 } cloud_server_counters;
 
-/* ---- status ------------------------------------------------------------  * Library plumbing; no counterpart in the paper.
- */
+/* ---- status ------------------------------------------------------------ */
+
+/* Name of a status code (library plumbing; no counterpart in the paper). */
 const char *cloud_status_string(int status);
 /* Last failure on the calling thread ("" if none). */
 const char *cloud_last_error_message(void);
@@ -179,14 +180,16 @@ const char *cloud_last_error_message(void);
  * `stream` has passed the generation work.  *out is set only on success. */
 int cloud_volume_create(const cloud_volume_desc *desc, void *stream, cloud_volume **out);
 
-/* Frees a volume.  The caller guarantees that no enqueued work still uses it.  * (Volume lifetime; the tiles are those of cloud_volume_create, Sec. 1.)
+/* Frees a volume.  The caller guarantees that no enqueued work still uses it.
+ * (Volume lifetime; the tiles are those of cloud_volume_create, Sec. 1.)
  */
 int cloud_volume_destroy(cloud_volume *vol);
 
 /* Copies the noise tiles into caller-owned device buffers as float values
  * in [0, 1) (decoding reduced-precision storage): base base_n^3, detail
  * detail_n^3, weather weather_n^2, x fastest.  Any pointer may be NULL to
- * skip that tile.  For tests and tools.  * (The density tiles of Sec. 1, decoded for checks.)
+ * skip that tile.  For tests and tools.
+ * (The density tiles of Sec. 1, decoded for checks.)
  */
 int cloud_volume_export(const cloud_volume *vol, float *base, float *detail, float *weather,
                         void *stream);
@@ -214,7 +217,8 @@ int cloud_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_p
 
 /* As cloud_render, and also adds the number of density evaluations the
  * launch performed to *lookups (device, one uint64, caller-owned; the caller
- * zeroes it).  Measures the effective work of a frame.  * (The lookups are the density samples of Sec. 1: one per view step
+ * zeroes it).  Measures the effective work of a frame.
+ * (The lookups are the density samples of Sec. 1: one per view step
  * plus one per light step of each step with density.)
  */
 int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
@@ -234,20 +238,21 @@ int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const c
  * storage precision and light-step count (later cloud_render, new batches and
  * new servers use it), and returns it in *best (and the per-configuration mean
  * times in times_ms[CLOUD_TUNE_CONFIGS] if not NULL).  Waits for the stream. */
-/* Reads / sets the launch configuration that cloud_render, new batches and
- * new servers use for volumes of `precision` rendered with `light_steps`
- * light steps (e.g. to restore a configuration an earlier autotune found).
- * config outside [0, CLOUD_TUNE_CONFIGS) or a bad precision is
- * CLOUD_ERR_INVALID_ARG.  Process-wide; host only.  * Scheduling only; no counterpart in the paper (the pixel results do not
- * depend on it).
- */
-int cloud_get_launch_config(int precision, int light_steps, int *config);
-int cloud_set_launch_config(int precision, int light_steps, int config);
-
 int cloud_autotune_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_params *prm,
                           int width, int height, int steps, int light_steps, int jitter_frame,
                           int integration, float *out_rgba, int repeats, float *times_ms,
                           int *best, void *stream);
+
+/* Reads / sets the launch configuration that cloud_render, new batches and
+ * new servers use for volumes of `precision` rendered with `light_steps`
+ * light steps (e.g. to restore a configuration an earlier autotune found).
+ * config outside [0, CLOUD_TUNE_CONFIGS) or a bad precision is
+ * CLOUD_ERR_INVALID_ARG.  Process-wide; host only.
+ * Scheduling only; no counterpart in the paper (the pixel results do not
+ * depend on it).
+ */
+int cloud_get_launch_config(int precision, int light_steps, int *config);
+int cloud_set_launch_config(int precision, int light_steps, int config);
 
 /* ---- multi-view batches (each view as cloud_render) --------------------- */
 
@@ -256,7 +261,8 @@ int cloud_autotune_render(const cloud_volume *vol, const cloud_camera *cam, cons
  * the views' pixel tiles form a work queue (longest step counts first) that
  * resident CTAs drain through a device counter.  The library allocates and
  * owns the view table and the counter.  Each view's output equals a
- * cloud_render of that view.  * (Each view is the raymarch of Sec. 1 / Sec. 3.1 / Sec. 3.2 exactly as
+ * cloud_render of that view.
+ * (Each view is the raymarch of Sec. 1 / Sec. 3.1 / Sec. 3.2 exactly as
  * cloud_render; batching itself has no counterpart in the paper.)
  */
 int cloud_batch_create(const cloud_volume *vol, const cloud_params *prm, int light_steps,
@@ -284,7 +290,7 @@ int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms, int *best
  * where cudaMalloc/cudaFree may block, synchronize the device or fail.
  * The caller still owns every view's out_rgba.  The scratch (work counter and
  * view table) is one library-wide static device array sized for
- * CLOUD_STATIC_MAX_VIEWS (256) views, 45312 bytes, which every GPU that loads
+ * CLOUD_STATIC_MAX_VIEWS (256) views, 47360 bytes, which every GPU that loads
  * the library holds until the process exits; n_views above 256 returns
  * CLOUD_ERR_INVALID_ARG.  The first call on a device looks up that array's
  * device address (a runtime query), so make it before any stream capture.
@@ -300,7 +306,8 @@ int cloud_batch_render_static(const cloud_volume *vol, const cloud_params *prm, 
  * each pixel of camera `cur` relative to camera `prev`: the pixel's ray
  * entry point into the cloud layer (or the point at t_max for rays that do
  * not enter it ahead of the camera) is projected into `prev`;
- * motion = pixel centre - that projection.  Points behind `prev` get 1e9.  * (The per-pixel reprojection the TAA of Sec. 3.2 needs.)
+ * motion = pixel centre - that projection.  Points behind `prev` get 1e9.
+ * (The per-pixel reprojection the TAA of Sec. 3.2 needs.)
  */
 int cloud_motion(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                  const cloud_camera *cur, int width, int height, float *motion, void *stream);
@@ -324,7 +331,8 @@ int taa_resolve(const void *history, const float *current, const float *motion,
  * may then be NULL).  Buffers as in taa_resolve; `current` is read through a
  * TMA tensor map built for this call (width*height contiguous float4), so it
  * must stay valid until the launch completes.  Results are bitwise those of
- * cloud_motion + taa_resolve.  * (Sec. 3.2: reprojection and the TAA resolve.)
+ * cloud_motion + taa_resolve.
+ * (Sec. 3.2: reprojection and the TAA resolve.)
  */
 int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                         const cloud_camera *cur, const void *history, const float *current,
@@ -340,10 +348,15 @@ int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const 
 int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width, int cloud_height,
                     const float *background, float *out, int width, int height, void *stream);
 
-/* Number of bounded device-side waits that gave up since the last reset (a
- * bulk copy into shared memory that did not complete; the affected tile's
- * outputs are left unwritten instead of waiting without limit).  Zero in
- * normal operation.  Synchronous; reset != 0 clears the counter.  * Failure reporting; no counterpart in the paper.
+/* Number of bounded device-side waits that gave up since the last reset,
+ * over every launch of the library in this process.  The fused resolve
+ * brings its current-frame tile into shared memory with one bulk copy and
+ * waits for it a bounded number of polls; if the copy has not landed by then
+ * the tile's outputs are left unwritten (no wait is unbounded) and the
+ * give-up is counted here and, for session and server frames, reported by
+ * those calls as CLOUD_ERR_TIMEOUT.  Zero in normal operation.  Synchronous;
+ * reset != 0 clears the counter.
+ * Failure reporting; no counterpart in the paper.
  */
 int cloud_device_wait_timeouts(unsigned int *count, int reset);
 
@@ -355,6 +368,14 @@ int cloud_device_wait_timeouts(unsigned int *count, int reset);
 int cloud_session_create(const cloud_volume *vol, int width, int height, int history_fmt,
                          cloud_session **out);
 int cloud_session_destroy(cloud_session *s);
+
+/* Failure reporting shared by the session calls below: if a bounded wait in
+ * one of this session's resolves gave up (cloud_device_wait_timeouts), a tile
+ * of the resolved frame and so of the history was not written.  The first
+ * session call that observes it (cloud_session_frame with host_out, after it
+ * waits; any later frame call; cloud_session_wait_frame) returns
+ * CLOUD_ERR_TIMEOUT, and every frame call does so without rendering until
+ * cloud_session_reset. */
 
 /* One frame of Sec. 3.2: render with jitter_frame = the session's frame
  * index, then the fused reprojection (motion from the previous frame's
@@ -381,7 +402,8 @@ int cloud_session_frame_async(cloud_session *s, const cloud_camera *cam, const c
  * issued by cloud_session_frame_async. */
 int cloud_session_wait_frame(cloud_session *s, int frame_index, int timeout_ms);
 
-/* Forgets the history: the next frame is a first frame (index kept). */
+/* Forgets the history: the next frame is a first frame (index kept); also
+ * clears a CLOUD_ERR_TIMEOUT state. */
 int cloud_session_reset(cloud_session *s);
 
 /* ---- continuous-batching render server ----------------------------------- */
@@ -406,13 +428,17 @@ int cloud_server_destroy(cloud_server *srv);
  * jitter index live on the device. */
 int cloud_server_open_session(cloud_server *srv, int width, int height, int *session_id);
 /* Frees a session with no queued request; waits (at most 10 s) for an
- * in-flight frame. */
+ * in-flight frame.  From the start of the call cloud_server_submit refuses
+ * the session. */
 int cloud_server_close_session(cloud_server *srv, int session_id);
 /* Queues the next frame of a session (camera, view steps); returns at once. */
 int cloud_server_submit(cloud_server *srv, int session_id, const cloud_camera *cam, int steps,
                         uint64_t *ticket);
 /* Waits at most timeout_ms for a request (CLOUD_ERR_TIMEOUT otherwise), then
- * returns its timing and forgets the ticket. */
+ * returns its timing and forgets the ticket.  A request whose batch had a
+ * resolve wait give up (cloud_device_wait_timeouts) also ends with
+ * CLOUD_ERR_TIMEOUT (ticket forgotten); its session's next frame is then a
+ * first frame. */
 int cloud_server_wait(cloud_server *srv, uint64_t ticket, int timeout_ms, cloud_request_info *info);
 /* Device address of a session's latest resolved frame (history format),
  * NULL before its first frame; invalid while a frame of it is in flight. */
@@ -429,9 +455,19 @@ int cloud_server_stats(cloud_server *srv, cloud_server_counters *st);
 
 /* out[i] = hash(keys[4i], keys[4i+1], keys[4i+2], keys[4i+3]) on the device
  * (the counter-based hash of the jitter and the noise lattice).  keys and
- * out are device buffers of 4n and n uint32.  * (The counter-based hash behind the Sec. 3.2 offsets and the noise lattice.)
+ * out are device buffers of 4n and n uint32.
+ * (The counter-based hash behind the Sec. 3.2 offsets and the noise lattice.)
  */
 int cloud_hash4_batch(const uint32_t *keys, int64_t n, uint32_t *out, void *stream);
+
+/* Sets how many times the fused resolve polls for its tile copy before it
+ * gives up (the first of its two bounded waits; < 0 restores the default of
+ * 65536, at most 2^30), for launches issued after the call.  For tests of
+ * the failure reporting: with 0 every tile gives up at once, the copy still
+ * lands within the second bounded wait, and the tiles' outputs stay
+ * unwritten.  Process-wide.
+ * Failure reporting; no counterpart in the paper. */
+int cloud_debug_set_wait_polls(int first_polls);
 
 #ifdef __cplusplus
 }

@@ -289,6 +289,13 @@ def device_wait_timeouts(reset: bool = False) -> int:
     return n.value
 
 
+def set_wait_polls(first_polls: int = -1):
+    """Poll budget of the fused resolve's first bounded wait for its tile copy
+    (cloud_debug_set_wait_polls; -1 restores the default).  For tests of the
+    failure reporting."""
+    N.check(N.lib().cloud_debug_set_wait_polls(int(first_polls)), "cloud_debug_set_wait_polls")
+
+
 def launch_config(precision: str, light_steps: int) -> int:
     """The launch configuration renders of this precision and light-step count
     use (cloud_get_launch_config)."""

@@ -254,6 +254,8 @@ extern "C" int cloud_batch_autotune(cloud_batch *b, int repeats, float *times_ms
 namespace {
 constexpr size_t kStaticTableOffset = 256;  // the counter sits in the first 256 bytes
 constexpr size_t kStaticBytes = kStaticTableOffset + sizeof(ViewParams) * CLOUD_STATIC_MAX_VIEWS;
+// the documented size of the array (include/cloudvol.h); fails to compile if ViewParams changes
+static_assert(kStaticBytes == 47360, "static scratch size changed: update its documentation");
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void *g_static_addr[kMaxDevices] = {};

@@ -234,9 +234,11 @@ struct ResolveRequest {
 };
 // Builds the per-view table in h_table (pinned host, resolve_view_bytes() per
 // view), uploads it to d_table on s and launches one kernel over all views.
+// status (device or mapped host memory, may be NULL) counts the launch's
+// bounded waits that gave up.
 int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
                                const ResolveRequest *reqs, int n, int fmt, float blend,
-                               void *h_table, void *d_table, cudaStream_t s);
+                               void *h_table, void *d_table, unsigned int *status, cudaStream_t s);
 size_t resolve_view_bytes();
 
 // Plain (unpacked) texel loads, decoded to the centred value.

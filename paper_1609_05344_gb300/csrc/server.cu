@@ -55,6 +55,7 @@ struct Session {
     cloud_camera prev_cam{};
     bool busy = false;  // a frame of this session is in flight
     bool open = false;
+    bool closing = false;  // cloud_server_close_session is waiting for it: no new requests
     size_t bytes = 0;
 };
 
@@ -75,6 +76,10 @@ struct Slot {
     void *h_rtable = nullptr;       // pinned: the resolve's per-view table
     void *d_rtable = nullptr;
     unsigned int *d_work = nullptr;
+    // bounded waits of this slot's resolves that gave up: mapped pinned host
+    // counter (never reset) and the value last accounted for
+    unsigned int *h_wait = nullptr, *d_wait = nullptr;
+    unsigned int wait_seen = 0;
     bool busy = false;
     std::vector<uint64_t> reqs;
     std::vector<ResolveRequest> resolves;
@@ -118,13 +123,20 @@ void CUDART_CB on_slot_done(void *arg) {
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         Slot &sl = srv->slots[c->slot];
+        // a resolve tile that gave up its bounded wait was left unwritten: the
+        // batch's requests fail with CLOUD_ERR_TIMEOUT and their sessions'
+        // next frames start without history
+        const unsigned int waits = *reinterpret_cast<volatile unsigned int *>(sl.h_wait);
+        const bool gave_up = waits != sl.wait_seen;
+        sl.wait_seen = waits;
         for (uint64_t id : sl.reqs) {
             auto it = srv->requests.find(id);
             if (it == srv->requests.end()) continue;
             Request &r = *it->second;
             r.t_done = t;
-            r.status = 2;
+            r.status = gave_up ? CLOUD_ERR_TIMEOUT : 2;
             srv->sessions[r.session].busy = false;
+            if (gave_up) srv->sessions[r.session].has_history = false;
             ++srv->completed;
         }
         sl.reqs.clear();
@@ -175,7 +187,7 @@ int launch_slot(cloud_server *srv, int si, const std::vector<Request *> &batch) 
     }
     if (int rc = launch_taa_reproject_batch(srv->vol, &srv->prm, sl.resolves.data(), n,
                                             srv->cfg.history_fmt, srv->cfg.blend, sl.h_rtable,
-                                            sl.d_rtable, sl.stream))
+                                            sl.d_rtable, sl.d_wait, sl.stream))
         return rc;
     for (const Request *rp : batch) {
         // the session stays busy until this slot completes, so its state can advance now
@@ -220,6 +232,14 @@ void worker_main(cloud_server *srv) {
              it != srv->queue.end() && (int)batch.size() < srv->cfg.max_batch_views;) {
             Request *r = srv->requests[*it].get();
             Session &se = srv->sessions[r->session];
+            if (!se.open) {
+                // cannot happen while close_session refuses sessions with queued
+                // requests; fail the request rather than render into freed buffers
+                r->status = CLOUD_ERR_INVALID_ARG;
+                it = srv->queue.erase(it);
+                srv->cv.notify_all();
+                continue;
+            }
             if (!se.busy) {
                 se.busy = true;  // also excludes a second request of this session
                 batch.push_back(r);
@@ -304,6 +324,14 @@ extern "C" int cloud_server_create(const cloud_volume *vol, const cloud_params *
         if (!rc)
             rc = check_cuda(cudaMalloc(&sl.d_rtable, resolve_view_bytes() * cfg->max_batch_views),
                             "cudaMalloc resolve table");
+        if (!rc)
+            rc = check_cuda(cudaHostAlloc((void **)&sl.h_wait, sizeof(unsigned int), cudaHostAllocMapped),
+                            "cudaHostAlloc wait counter");
+        if (!rc) {
+            *sl.h_wait = 0;
+            rc = check_cuda(cudaHostGetDevicePointer((void **)&sl.d_wait, sl.h_wait, 0),
+                            "cudaHostGetDevicePointer wait counter");
+        }
     }
     if (!rc) {
         try {
@@ -320,6 +348,7 @@ extern "C" int cloud_server_create(const cloud_volume *vol, const cloud_params *
             if (sl.d_work) cudaFree(sl.d_work);
             if (sl.h_rtable) cudaFreeHost(sl.h_rtable);
             if (sl.d_rtable) cudaFree(sl.d_rtable);
+            if (sl.h_wait) cudaFreeHost(sl.h_wait);
         }
         delete srv;
         return rc;
@@ -345,6 +374,7 @@ extern "C" int cloud_server_destroy(cloud_server *srv) {
         cudaFree(sl.d_work);
         cudaFreeHost(sl.h_rtable);
         cudaFree(sl.d_rtable);
+        cudaFreeHost(sl.h_wait);
     }
     for (auto &se : srv->sessions)
         if (se.open) free_session_buffers(se);
@@ -398,14 +428,27 @@ extern "C" int cloud_server_close_session(cloud_server *srv, int session_id) {
     clear_error();
     if (!srv) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_server_close_session: null server");
     std::unique_lock<std::mutex> lk(srv->mu);
-    if (session_id < 0 || session_id >= (int)srv->sessions.size() || !srv->sessions[session_id].open)
+    if (session_id < 0 || session_id >= (int)srv->sessions.size() || !srv->sessions[session_id].open ||
+        srv->sessions[session_id].closing)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_server_close_session: no such session");
     for (uint64_t id : srv->queue)
         if (srv->requests[id]->session == session_id)
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_server_close_session: requests still queued");
+    // from here on cloud_server_submit refuses this session, so the queue
+    // cannot gain a request for it while the wait below releases the lock
+    srv->sessions[session_id].closing = true;
     if (!srv->cv.wait_for(lk, std::chrono::seconds(10),
-                          [&] { return !srv->sessions[session_id].busy || srv->error; }))
+                          [&] { return !srv->sessions[session_id].busy || srv->error; })) {
+        srv->sessions[session_id].closing = false;
         return set_error(CLOUD_ERR_TIMEOUT, "cloud_server_close_session: frame still in flight");
+    }
+    if (srv->sessions[session_id].busy) {
+        // the server failed with a frame of this session still enqueued: let
+        // the slot streams drain before the buffers they use are freed
+        lk.unlock();
+        for (auto &sl : srv->slots) cudaStreamSynchronize(sl.stream);
+        lk.lock();
+    }
     free_session_buffers(srv->sessions[session_id]);
     return CLOUD_OK;
 }
@@ -420,7 +463,8 @@ extern "C" int cloud_server_submit(cloud_server *srv, int session_id, const clou
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if (srv->error) return set_error(srv->error, "cloud_server_submit: server failed: " + srv->error_msg);
-        if (session_id < 0 || session_id >= (int)srv->sessions.size() || !srv->sessions[session_id].open)
+        if (session_id < 0 || session_id >= (int)srv->sessions.size() || !srv->sessions[session_id].open ||
+            srv->sessions[session_id].closing)
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_server_submit: no such session");
         r->id = srv->next_id++;
         r->session = session_id;
@@ -446,7 +490,14 @@ extern "C" int cloud_server_wait(cloud_server *srv, uint64_t ticket, int timeout
     const bool ok = srv->cv.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)),
                                      [&] { return r->status == 2 || r->status < 0; });
     if (!ok) return set_error(CLOUD_ERR_TIMEOUT, "cloud_server_wait: request not finished in time");
-    if (r->status < 0) return set_error(r->status, "cloud_server_wait: " + srv->error_msg);
+    if (r->status < 0) {
+        const int st = r->status;
+        srv->requests.erase(it);
+        if (st == CLOUD_ERR_TIMEOUT)
+            return set_error(st, "cloud_server_wait: a bounded wait of this frame's TAA resolve gave "
+                                 "up; the frame misses a tile and the session's history was reset");
+        return set_error(st, "cloud_server_wait: " + srv->error_msg);
+    }
     if (info) {
         info->session = r->session;
         info->steps = r->steps;

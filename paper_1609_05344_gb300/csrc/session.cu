@@ -5,6 +5,7 @@
 // per-frame jitter; a frame is render -> (motion + TAA resolve, fused) -> swap.
 #include <chrono>
 #include <cstring>
+#include <string>
 #include <new>
 #include <thread>
 
@@ -17,7 +18,7 @@ int launch_render(const cloud_volume *vol, const cloud_camera *cam, const cloud_
 int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                          const cloud_camera *cur, const void *history, const float *current,
                          void *history_out, int width, int height, int fmt, float blend,
-                         cudaStream_t s);
+                         unsigned int *status, cudaStream_t s);
 }  // namespace cloudvol
 
 struct cloud_session {
@@ -36,6 +37,14 @@ struct cloud_session {
     cudaEvent_t resolved[2], copied[2];
     bool copy_pending[2];
     int copy_frame[2];  // frame index whose copy was last issued from hist[i]
+    // bounded waits of this session's resolves that gave up: a counter in
+    // mapped pinned host memory the resolve kernel increments (never reset, so
+    // no reset can race with a kernel in flight); wait_seen is the value last
+    // accounted for.  A give-up leaves a tile of the history unwritten, so the
+    // session reports CLOUD_ERR_TIMEOUT until cloud_session_reset.
+    unsigned int *h_wait, *d_wait;
+    unsigned int wait_seen;
+    bool wait_failed;
 };
 
 using namespace cloudvol;
@@ -52,7 +61,23 @@ void free_session(cloud_session *s) {
     if (s->current) cudaFree(s->current);
     if (s->hist[0]) cudaFree(s->hist[0]);
     if (s->hist[1]) cudaFree(s->hist[1]);
+    if (s->h_wait) cudaFreeHost(s->h_wait);
     delete s;
+}
+
+// CLOUD_ERR_TIMEOUT once a resolve of this session has given up a bounded
+// wait (seen through the mapped counter), until cloud_session_reset.
+int check_waits(cloud_session *s, const char *where) {
+    const unsigned int v = *reinterpret_cast<volatile unsigned int *>(s->h_wait);
+    if (v != s->wait_seen) {
+        s->wait_seen = v;
+        s->wait_failed = true;
+    }
+    if (s->wait_failed)
+        return set_error(CLOUD_ERR_TIMEOUT, std::string(where) +
+                                                ": a bounded wait of the TAA resolve gave up, the "
+                                                "history misses a tile until cloud_session_reset");
+    return CLOUD_OK;
 }
 }  // namespace
 
@@ -77,6 +102,13 @@ extern "C" int cloud_session_create(const cloud_volume *vol, int width, int heig
     if (!rc) rc = check_cuda(cudaMalloc(&s->hist[1], hb), "cudaMalloc history");
     if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking),
                              "cudaStreamCreate");
+    if (!rc) rc = check_cuda(cudaHostAlloc((void **)&s->h_wait, sizeof(unsigned int), cudaHostAllocMapped),
+                             "cudaHostAlloc wait counter");
+    if (!rc) {
+        *s->h_wait = 0;
+        rc = check_cuda(cudaHostGetDevicePointer((void **)&s->d_wait, s->h_wait, 0),
+                        "cudaHostGetDevicePointer wait counter");
+    }
     for (int i = 0; i < 2 && !rc; ++i) {
         rc = check_cuda(cudaEventCreateWithFlags(&s->resolved[i], cudaEventDisableTiming), "cudaEventCreate");
         if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming), "cudaEventCreate");
@@ -101,6 +133,8 @@ extern "C" int cloud_session_reset(cloud_session *s) {
     clear_error();
     if (!s) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_reset: null session");
     s->has_history = false;
+    s->wait_seen = *reinterpret_cast<volatile unsigned int *>(s->h_wait);
+    s->wait_failed = false;
     return CLOUD_OK;
 }
 
@@ -121,7 +155,7 @@ int session_render(cloud_session *s, const cloud_camera *cam, const cloud_params
     // reprojection motion and TAA resolve fused (the motion is never stored)
     rc = launch_taa_reproject(s->vol, prm, s->has_history ? &s->prev_cam : nullptr, cam,
                               s->has_history ? s->hist[s->latest] : nullptr, s->current,
-                              s->hist[next], s->width, s->height, s->fmt, blend, st);
+                              s->hist[next], s->width, s->height, s->fmt, blend, s->d_wait, st);
     if (rc) return rc;
     s->latest = next;
     s->has_history = true;
@@ -142,6 +176,7 @@ extern "C" int cloud_session_frame(cloud_session *s, const cloud_camera *cam,
                                    const void **dev_out, void *stream) {
     clear_error();
     if (!s || !cam || !prm) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_frame: null pointer");
+    if (int rc = check_waits(s, "cloud_session_frame")) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     int written = 0;
     int rc = session_render(s, cam, prm, steps, light_steps, integration, blend, st, &written);
@@ -153,6 +188,7 @@ extern "C" int cloud_session_frame(cloud_session *s, const cloud_camera *cam,
                         "cudaMemcpyAsync resolved frame");
         if (rc) return rc;
         rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        if (!rc) rc = check_waits(s, "cloud_session_frame");
     }
     return rc;
 }
@@ -164,6 +200,7 @@ extern "C" int cloud_session_frame_async(cloud_session *s, const cloud_camera *c
     clear_error();
     if (!s || !cam || !prm || !host_out)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_frame_async: null pointer");
+    if (int rc = check_waits(s, "cloud_session_frame_async")) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int index = s->frame;
     int written = 0;
@@ -199,7 +236,7 @@ extern "C" int cloud_session_wait_frame(cloud_session *s, int frame_index, int t
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {  // bounded host-side polling of the copy's completion event
         const cudaError_t q = cudaEventQuery(s->copied[slot]);
-        if (q == cudaSuccess) return CLOUD_OK;
+        if (q == cudaSuccess) return check_waits(s, "cloud_session_wait_frame");
         if (q != cudaErrorNotReady) return check_cuda(q, "cudaEventQuery");
         if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
             return set_error(CLOUD_ERR_TIMEOUT, "cloud_session_wait_frame: read-back not finished");

@@ -9,6 +9,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -221,18 +222,28 @@ constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
 #define CLOUDVOL_TAA_MIN_BLOCKS 3  // CTAs per SM the fused kernel is compiled for (74 registers)
 #endif
 
-// Waits that gave up (a bulk copy that never completed): counted on the
-// device, read by cloud_device_wait_timeouts.  Every wait below is bounded.
+// Waits that gave up (a bulk copy that did not complete in time): counted on
+// the device, read by cloud_device_wait_timeouts; a launch may also be given a
+// counter of its own (`status`, device or mapped host memory) that its caller
+// reads.  Every wait below is bounded.  The first wait polls `first_polls`
+// times (kWaitPolls by default; cloud_debug_set_wait_polls changes it for
+// tests); after a give-up one thread waits once more, at most kDrainPolls
+// polls with a short sleep between them (about 0.1 s), for the copy already
+// issued, so that it lands before the block exits.
 __device__ unsigned int g_wait_timeouts = 0;
 constexpr int kWaitPolls = 1 << 16;
+constexpr int kDrainPolls = 1 << 20;
+std::atomic<int> g_first_polls{kWaitPolls};
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
-// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(const uint64_t *bar, unsigned parity) {
+// Bounded wait for phase `parity` of an mbarrier: at most `polls` polls
+// (with a sleep of `sleep_ns` between them); false when it gave up.
+__device__ __forceinline__ bool mbar_wait(const uint64_t *bar, unsigned parity, int polls,
+                                          unsigned sleep_ns = 0) {
     const unsigned a = smem_addr(bar);
-    for (int it = 0; it < kWaitPolls; ++it) {
+    for (int it = 0; it < polls; ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -241,6 +252,7 @@ __device__ __forceinline__ bool mbar_wait(const uint64_t *bar, unsigned parity) 
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (sleep_ns) __nanosleep(sleep_ns);
     }
     return false;
 }
@@ -253,7 +265,8 @@ template <typename H>
 __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const MotionParams &mp,
                                              const H *__restrict__ hist, H *__restrict__ out,
                                              float blend, int bx, int by,
-                                             float4 (&tile)[kTH + 2][kTW + 2], uint64_t &bar) {
+                                             float4 (&tile)[kTH + 2][kTW + 2], uint64_t &bar,
+                                             int first_polls, unsigned int *status) {
     const int W = mp.width, Hh = mp.height;
     const int x0 = bx * kTW, y0 = by * kTH;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -319,14 +332,20 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
             use[r] = true;
         }
     }
-    const bool landed = mbar_wait(&bar, 0);
+    const bool landed = mbar_wait(&bar, 0, first_polls);
     if (!__syncthreads_and(landed)) {
-        // the copy did not complete within the bounded wait: count it, give the
-        // copy one more bounded wait so that it cannot land after the CTA exits,
-        // and leave the outputs of this tile unwritten
+        // the copy did not complete within the bounded wait: count it (globally
+        // and in the launch's own counter), leave the outputs of this tile
+        // unwritten, and give the copy already issued one more bounded wait
+        // (about 0.1 s) before the block exits; if that wait also gives up the
+        // copy may still be pending, which counts a second time
         if (tid == 0) {
             atomicAdd(&g_wait_timeouts, 1u);
-            mbar_wait(&bar, 0);
+            if (status) atomicAdd_system(status, 1u);
+            if (!mbar_wait(&bar, 0, kDrainPolls, 100)) {
+                atomicAdd(&g_wait_timeouts, 1u);
+                if (status) atomicAdd_system(status, 1u);
+            }
         }
         return;
     }
@@ -375,10 +394,11 @@ template <typename H>
 __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
     taa_reproject_kernel(const __grid_constant__ CUtensorMap tile_map,
                          const __grid_constant__ MotionParams mp, const H *__restrict__ hist,
-                         H *__restrict__ out, float blend) {
+                         H *__restrict__ out, float blend, int first_polls, unsigned int *status) {
     __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
     __shared__ __align__(8) uint64_t bar;
-    resolve_tile<H>(&tile_map, mp, hist, out, blend, blockIdx.x, blockIdx.y, tile, bar);
+    resolve_tile<H>(&tile_map, mp, hist, out, blend, blockIdx.x, blockIdx.y, tile, bar, first_polls,
+                    status);
 }
 
 // Many views' resolves in one launch (the render server's batches): block b
@@ -396,7 +416,8 @@ struct alignas(64) ResolveView {
 
 template <typename H>
 __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
-    taa_reproject_batch_kernel(const ResolveView *__restrict__ views, int n_views) {
+    taa_reproject_batch_kernel(const ResolveView *__restrict__ views, int n_views, int first_polls,
+                               unsigned int *status) {
     __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ MotionParams smp;
@@ -419,7 +440,7 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
     __syncthreads();
     const int local = t - rv.tile_begin;
     resolve_tile<H>(&rv.map, smp, (const H *)rv.hist, (H *)rv.out, rv.blend, local % rv.tiles_x,
-                    local / rv.tiles_x, tile, bar);
+                    local / rv.tiles_x, tile, bar, first_polls, status);
 }
 
 int build_motion_params(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
@@ -551,7 +572,7 @@ static int current_tile_map(const float *current, int width, int height, CUtenso
 int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const cloud_camera *prev,
                          const cloud_camera *cur, const void *history, const float *current,
                          void *history_out, int width, int height, int fmt, float blend,
-                         cudaStream_t s) {
+                         unsigned int *status, cudaStream_t s) {
     if (!vol || !prm || !cur || !current || !history_out || (history && !prev))
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: null pointer");
     if (fmt != CLOUD_HISTORY_FP32 && fmt != CLOUD_HISTORY_FP16)
@@ -571,18 +592,22 @@ int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const
     CUtensorMap map;
     if (int rc = current_tile_map(current, width, height, &map)) return rc;
     const dim3 grid((width + kTW - 1) / kTW, (height + kTH - 1) / kTH), block(32, 8);
+    const int polls = g_first_polls.load();
     if (fmt == CLOUD_HISTORY_FP32)
         taa_reproject_kernel<float4><<<grid, block, 0, s>>>(map, p, (const float4 *)history,
-                                                            (float4 *)history_out, blend);
+                                                            (float4 *)history_out, blend, polls,
+                                                            status);
     else
         taa_reproject_kernel<uint2><<<grid, block, 0, s>>>(map, p, (const uint2 *)history,
-                                                           (uint2 *)history_out, blend);
+                                                           (uint2 *)history_out, blend, polls,
+                                                           status);
     return check_launch("taa_reproject_kernel");
 }
 
 int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
                                const ResolveRequest *reqs, int n, int fmt, float blend,
-                               void *h_table_v, void *d_table_v, cudaStream_t s) {
+                               void *h_table_v, void *d_table_v, unsigned int *status,
+                               cudaStream_t s) {
     if (!vol || !prm || !reqs || n < 1 || !h_table_v || !d_table_v)
         return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: bad arguments");
     if (fmt != CLOUD_HISTORY_FP32 && fmt != CLOUD_HISTORY_FP16)
@@ -621,10 +646,11 @@ int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
                             "resolve batch: upload table"))
         return rc;
     const ResolveView *d_table = static_cast<const ResolveView *>(d_table_v);
+    const int polls = g_first_polls.load();
     if (fmt == CLOUD_HISTORY_FP32)
-        taa_reproject_batch_kernel<float4><<<next, dim3(32, 8), 0, s>>>(d_table, n);
+        taa_reproject_batch_kernel<float4><<<next, dim3(32, 8), 0, s>>>(d_table, n, polls, status);
     else
-        taa_reproject_batch_kernel<uint2><<<next, dim3(32, 8), 0, s>>>(d_table, n);
+        taa_reproject_batch_kernel<uint2><<<next, dim3(32, 8), 0, s>>>(d_table, n, polls, status);
     return check_launch("taa_reproject_batch_kernel");
 }
 
@@ -711,7 +737,7 @@ extern "C" int cloud_taa_reproject(const cloud_volume *vol, const cloud_params *
                                    void *stream) {
     clear_error();
     return launch_taa_reproject(vol, prm, prev, cur, history, current, history_out, width, height,
-                                history_fmt, blend, (cudaStream_t)stream);
+                                history_fmt, blend, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int cloud_composite(const void *cloud, int cloud_fmt, int cloud_width, int cloud_height,
@@ -733,5 +759,13 @@ extern "C" int cloud_device_wait_timeouts(unsigned int *count, int reset) {
         return check_cuda(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(unsigned int)),
                           "cloud_device_wait_timeouts");
     }
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_debug_set_wait_polls(int first_polls) {
+    clear_error();
+    if (first_polls > (1 << 30))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_debug_set_wait_polls: more than 2^30 polls");
+    g_first_polls.store(first_polls < 0 ? kWaitPolls : first_polls);
     return CLOUD_OK;
 }

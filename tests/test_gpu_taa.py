@@ -194,14 +194,6 @@ def test_session_frame_device_view_and_buffer_checks(api):
         api.taa(None, torch.empty((48, 64, 4), device="cuda"), torch.empty((48, 64, 1), device="cuda"))
 
 
-def test_zz_no_device_wait_gave_up(api):
-    """Every bounded wait of the resolve kernels in this module's tests completed
-    (the tile copies all landed)."""
-    import torch
-    torch.cuda.synchronize()
-    assert api.device_wait_timeouts() == 0
-
-
 @pytest.mark.parametrize("jump", ["yaw-40", "behind", "translate-2km", "above-layer"])
 def test_fused_resolve_large_camera_jumps(api, oracle, jump):
     """Camera jumps that push much of the history off screen or behind the
@@ -288,3 +280,71 @@ def test_fused_resolve_random_camera_pairs(api, oracle):
         ref = oracle.taa(hist.astype(np.float64), cur.astype(np.float64), omot, blend=blend)
         worst = max(worst, float(np.abs(got.astype(np.float64) - ref).max()))
     assert worst <= 1e-4
+
+
+def test_resolve_wait_give_up_is_reported(api):
+    """The fused resolve's bounded wait for its tile copy, made to give up at
+    once (poll budget 0): every tile's outputs stay unwritten, the give-ups are
+    counted, a session reports CLOUD_ERR_TIMEOUT (sticky until reset) and a
+    server request fails with it.  The copy itself is a valid in-bounds load
+    that the kernel's second bounded wait still sees land before it exits."""
+    import torch
+    from paper_1609_05344_gb300 import _native as N
+    vol = api.Volume(I.volume_desc("tiny", seed=1))
+    prm = I.params()
+    w, h, tiles = 70, 37, 3 * 3  # 32x16-pixel tiles: 3 columns, 3 rows (ragged)
+    cams = [I.orbit_camera(f, 1) for f in range(3)]
+    torch.cuda.synchronize()
+    before = api.device_wait_timeouts()
+    cur0 = api.render(vol, cams[0], prm, w, h, 8, 6, jitter_frame=0)
+    cur1 = api.render(vol, cams[1], prm, w, h, 8, 6, jitter_frame=1)
+    hist0 = api.taa_reproject(vol, prm, None, cams[0], None, cur0)
+    host = torch.empty((h, w, 4), dtype=torch.float32, pin_memory=True)
+    sess, ref = api.Session(vol, w, h), api.Session(vol, w, h)
+    srv = api.Server(vol, prm, history_fmt="fp32", max_sessions=2, max_batch_views=4, slots=1,
+                     reserve_bytes=0)
+    sid = srv.open_session(w, h)
+    try:
+        api.set_wait_polls(0)
+        out = api.taa_reproject(vol, prm, cams[0], cams[1], hist0, cur1,
+                                out=torch.full((h, w, 4), -7.0, device="cuda"))
+        torch.cuda.synchronize()
+        assert api.device_wait_timeouts() - before == tiles
+        assert bool((out == -7.0).all())
+        with pytest.raises(N.CloudError) as e:
+            sess.frame(cams[0], prm, 8, 6, host_out=host)
+        assert e.value.status == N.ERR_TIMEOUT
+        with pytest.raises(N.CloudError) as e:  # sticky: refused without rendering
+            sess.frame(cams[1], prm, 8, 6, host_out=host)
+        assert e.value.status == N.ERR_TIMEOUT
+        with pytest.raises(N.CloudError) as e:
+            srv.wait(srv.submit(sid, cams[0], 8), 20000)
+        assert e.value.status == N.ERR_TIMEOUT
+    finally:
+        api.set_wait_polls(-1)
+    torch.cuda.synchronize()
+    assert api.device_wait_timeouts() - before == 3 * tiles
+    # after a reset the session continues exactly like one that never failed:
+    # frame index 1 as a first frame, then frame 2 with history
+    ref.frame(cams[0], prm, 8, 6, host_out=host)
+    ref.reset()
+    sess.reset()
+    for f in (1, 2):
+        a = sess.frame(cams[f], prm, 8, 6, host_out=torch.empty_like(host)).clone()
+        b = ref.frame(cams[f], prm, 8, 6, host_out=torch.empty_like(host)).clone()
+        assert torch.equal(a, b)
+    # the server session's next frame is a first frame and succeeds
+    srv.wait(srv.submit(sid, cams[1], 8), 20000)
+    srv.close()
+    sess.close()
+    ref.close()
+    if before == 0:
+        api.device_wait_timeouts(reset=True)
+
+
+def test_zz_no_device_wait_gave_up(api):
+    """Every bounded wait of the resolve kernels in this module's other tests
+    completed (the tile copies all landed)."""
+    import torch
+    torch.cuda.synchronize()
+    assert api.device_wait_timeouts() == 0
