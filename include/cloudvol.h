@@ -38,10 +38,15 @@ extern "C" {
 #define CLOUD_ERR_UNSUPPORTED (-5)   /* valid request this build does not provide    */
 
 /* ---- enumerations ------------------------------------------------------ */
-#define CLOUD_PRECISION_FP32 0 /* volume texels stored as float                  */
-#define CLOUD_PRECISION_FP16 1 /* volume texels stored as IEEE half              */
-#define CLOUD_PRECISION_BF16 2 /* volume texels stored as bfloat16               */
-#define CLOUD_PRECISION_UNORM16 3 /* texels as 16-bit fixed point v * 65536      */
+/* Storage of the noise tiles.  Tiles are kept as corner-packed records (the 8
+ * texels of a trilinear footprint, 4 of a bilinear one); the 16-bit formats
+ * halve the record bytes of FP32. */
+#define CLOUD_PRECISION_FP32 0    /* texels as float                                */
+#define CLOUD_PRECISION_FP16 1    /* corner 0 as 16-bit fixed point, the other
+                                     corners as IEEE half differences from it      */
+#define CLOUD_PRECISION_BF16 2    /* corner 0 as 16-bit fixed point, the other
+                                     corners as bfloat16 differences from it       */
+#define CLOUD_PRECISION_UNORM16 3 /* texels as 16-bit fixed point v * 65536         */
 
 #define CLOUD_DENSITY_NOISE 0    /* fBm base - detail, coverage remap, weather    */
 #define CLOUD_DENSITY_CONSTANT 1 /* constant density everywhere (closed forms)   */
@@ -193,6 +198,19 @@ int cloud_volume_destroy(cloud_volume *vol);
  */
 int cloud_volume_export(const cloud_volume *vol, float *base, float *detail, float *weather,
                         void *stream);
+
+/* Copies the volume's occupancy grid into `out` (device, `words` uint32,
+ * caller-owned): one bit per macro-cell of 2 x 2 x 2 base-tile texel cells,
+ * 2^(3 * *log2_cells) cells with x fastest, bit i of word i / 32 for cell i.
+ * A clear bit means the density is provably zero for every sample whose base
+ * record lies in the cell (the bound max B - detail_weight min Dt - coverage
+ * < 0 over its records); the raymarch then skips that lookup's memory reads,
+ * which changes no result.  With out == NULL only *log2_cells is set (-1 for
+ * a constant-density volume, which has no grid).  words must be
+ * ceil(2^(3 * *log2_cells) / 32).  For tests and tools.
+ * (Empty-space skipping for the density samples of Sec. 1.) */
+int cloud_volume_occupancy(const cloud_volume *vol, uint32_t *out, int64_t words, int *log2_cells,
+                           void *stream);
 
 /* ---- render (Sec. 1, Sec. 3.1, Sec. 3.2) -------------------------------- */
 
@@ -468,6 +486,13 @@ int cloud_hash4_batch(const uint32_t *keys, int64_t n, uint32_t *out, void *stre
  * unwritten.  Process-wide.
  * Failure reporting; no counterpart in the paper. */
 int cloud_debug_set_wait_polls(int first_polls);
+
+/* Turns the raymarch's use of the occupancy grid (cloud_volume_occupancy) off
+ * (enabled == 0) or back on, for launches issued after the call, so that tests
+ * can compare against the full evaluation of every lookup; the pixels are the
+ * same either way.  Process-wide; on by default.
+ * Scheduling only; no counterpart in the paper. */
+int cloud_debug_set_occupancy(int enabled);
 
 #ifdef __cplusplus
 }

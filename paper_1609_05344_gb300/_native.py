@@ -160,6 +160,8 @@ SIGNATURES = [
     ("cloud_session_wait_frame", _i, [_vp, _i, _i]),
     ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
     ("cloud_debug_set_wait_polls", _i, [_i]),
+    ("cloud_debug_set_occupancy", _i, [_i]),
+    ("cloud_volume_occupancy", _i, [_vp, _vp, ctypes.c_int64, _ip, _vp]),
     ("cloud_get_launch_config", _i, [_i, _i, _P(_i)]),
     ("cloud_set_launch_config", _i, [_i, _i, _i]),
     ("cloud_autotune_render", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, _i, _i, _i, _vp, _i,

@@ -86,6 +86,25 @@ class Volume:
         except Exception:
             pass
 
+    def occupancy(self, stream=None):
+        """The occupancy grid as a (C, C, C) bool numpy array indexed [z, y, x]
+        (cloud_volume_occupancy), or None for a constant-density volume."""
+        import numpy as np
+        lc = ctypes.c_int()
+        N.check(N.lib().cloud_volume_occupancy(self.handle, None, 0, ctypes.byref(lc),
+                                               _stream(stream)), "cloud_volume_occupancy")
+        if lc.value < 0:
+            return None
+        cells = 1 << (3 * lc.value)
+        words = torch.empty((cells + 31) // 32, dtype=torch.int32, device="cuda")
+        N.check(N.lib().cloud_volume_occupancy(self.handle, _ptr(words), words.numel(),
+                                               ctypes.byref(lc), _stream(stream)),
+                "cloud_volume_occupancy")
+        w = words.cpu().numpy().view(np.uint32)
+        bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:cells]
+        c = 1 << lc.value
+        return bits.astype(bool).reshape(c, c, c)
+
     def export(self, stream=None) -> dict:
         """Noise tiles as float32 CUDA tensors in [0, 1), indexed [z, y, x] / [y, x]."""
         d = self.desc
@@ -287,6 +306,11 @@ def device_wait_timeouts(reset: bool = False) -> int:
     N.check(N.lib().cloud_device_wait_timeouts(ctypes.byref(n), int(reset)),
             "cloud_device_wait_timeouts")
     return n.value
+
+
+def set_occupancy(enabled: bool = True):
+    """Use of the occupancy grid by the raymarch (cloud_debug_set_occupancy)."""
+    N.check(N.lib().cloud_debug_set_occupancy(1 if enabled else 0), "cloud_debug_set_occupancy")
 
 
 def set_wait_polls(first_polls: int = -1):

@@ -62,6 +62,10 @@ struct cloud_volume {
     void *base;      // device, base_n^3 corner-packed records of the storage precision
     void *detail;    // device or nullptr (detail_n^3 records)
     void *weather;   // device or nullptr (weather_n^2 records)
+    // occupancy grid: one bit per macro-cell of 2x2x2 base records (x fastest),
+    // clear where the density is provably 0 throughout (see build_occupancy)
+    uint32_t *occ;   // device or nullptr (constant density)
+    int log2_occ;    // macro-cells per axis = 2^log2_occ = base_n / 2
     int device;
 };
 
@@ -163,28 +167,54 @@ inline void split_df10(double v, float *hi, float *lo) {
 // (r, r+1) are the two z-neighbours a packed FP32x2 lerp works on; record k
 // of an N^2 tile holds the 4 texels of the bilinear footprint, r = 2 dx + dy.
 // One lookup is one contiguous record load (16 B for 16-bit texels, 32 B for
-// FP32) instead of 8 (or 4) scattered texel loads.  Texel k is entry 0.
+// FP32) instead of 8 (or 4) scattered texel loads.  Texels are stored centred
+// (fBm - 1/2).
 //
-// The loaders return the corners in an affine "raw" form r = texel + bias so
-// that a 16-bit fixed-point texel decodes with bit operations only; the
-// interpolated raw value minus `raw_bias<T>()` is the centred texel value.
-// They return the dx = 1 half of a record as differences from the dx = 0 half
-// (c[r + R/2] - c[r]), the operand the x lerp needs: FP32 records store them
-// so (packed once, rounded exactly as the lerp would), 16-bit loaders form
-// them after decoding.
-template <typename T>
-__host__ __device__ constexpr float raw_bias() { return 0.0f; }
-template <>
-__host__ __device__ constexpr float raw_bias<uint16_t>() { return 1.5f; }  // 1 + q 2^-16 = v + 1/2 + 1
+// Record formats, by storage precision:
+//   FP32     the texels, except that the dx = 1 half holds its differences
+//            from the dx = 0 half (rounded at packing exactly as the x lerp
+//            would round them);
+//   UNORM16  each texel as 16-bit fixed point q = round((t + 1/2) 2^16);
+//   FP16 / BF16  corner 0 as 16-bit fixed point (as UNORM16) and the other
+//            corners as IEEE half (bfloat16) differences from that decoded
+//            corner 0.  Neighbouring texels differ little, so the 11-bit (8-bit)
+//            significand rounds a small difference instead of the texel itself.
+// A loader returns the corners relative to an offset, with the dx = 1 half
+// as differences from the dx = 0 half (the operand the x lerp needs), and
+// returns the offset: the centred texel value at a point is the lerp of the
+// returned corners plus the offset (0 for FP32 records; -3/2 for UNORM16,
+// whose corners decode to 1 + q 2^-16 by bit operations; the decoded corner 0
+// for the difference records, whose corner 0 is then 0).
 
 // An FP32 record is one 32-byte sector, fetched by a single 256-bit load
 // (sm_100+ ld.global .v8): one L1 wavefront instead of two.
-__device__ __forceinline__ void load_rec8(const float *tile, uint32_t rec, float c[8]) {
+__device__ __forceinline__ float load_rec8(const float *tile, uint32_t rec, float c[8]) {
     const float *p = tile + 8 * (size_t)rec;
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]),
           "=f"(c[7])
         : "l"(p));
+    return 0.0f;
+}
+__device__ __forceinline__ float load_rec4(const float *tile, uint32_t rec, float c[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(tile) + rec);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    return 0.0f;
+}
+
+// 16-bit fields of a 32-bit word: 1 + q 2^-16 for fixed point (exact, bit
+// operations only); half and bfloat16 converted exactly.
+__device__ __forceinline__ float unorm_lo(uint32_t w) {
+    return __uint_as_float(0x3F800000u | ((w << 7) & 0x007FFF80u));
+}
+__device__ __forceinline__ float unorm_hi(uint32_t w) {
+    return __uint_as_float(0x3F800000u | ((w >> 9) & 0x007FFF80u));
+}
+__device__ __forceinline__ float f16_hi(uint32_t w, const __half *) {
+    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+}
+__device__ __forceinline__ float f16_hi(uint32_t w, const __nv_bfloat16 *) {
+    return __uint_as_float(w & 0xFFFF0000u);
 }
 __device__ __forceinline__ void unpack16(uint32_t w, const __half *, float &lo, float &hi) {
     const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
@@ -195,32 +225,50 @@ __device__ __forceinline__ void unpack16(uint32_t w, const __nv_bfloat16 *, floa
     lo = __uint_as_float(w << 16);
     hi = __uint_as_float(w & 0xFFFF0000u);
 }
-__device__ __forceinline__ void unpack16(uint32_t w, const uint16_t *, float &lo, float &hi) {
-    lo = __uint_as_float(0x3F800000u | ((w << 7) & 0x007FFF80u));  // 1 + q_lo 2^-16
-    hi = __uint_as_float(0x3F800000u | ((w >> 9) & 0x007FFF80u));  // 1 + q_hi 2^-16
-}
-template <typename T>
-__device__ __forceinline__ void load_rec8(const T *tile, uint32_t rec, float c[8]) {
+
+__device__ __forceinline__ float load_rec8(const uint16_t *tile, uint32_t rec, float c[8]) {
     const uint4 r = __ldg(reinterpret_cast<const uint4 *>(tile) + rec);
-    unpack16(r.x, tile, c[0], c[1]);
-    unpack16(r.y, tile, c[2], c[3]);
-    unpack16(r.z, tile, c[4], c[5]);
-    unpack16(r.w, tile, c[6], c[7]);
-    const float2 d0 = __fadd2_rn(make_float2(c[4], c[5]), make_float2(-c[0], -c[1]));
-    const float2 d1 = __fadd2_rn(make_float2(c[6], c[7]), make_float2(-c[2], -c[3]));
+    c[0] = unorm_lo(r.x); c[1] = unorm_hi(r.x);
+    c[2] = unorm_lo(r.y); c[3] = unorm_hi(r.y);
+    const float2 d0 = __fadd2_rn(make_float2(unorm_lo(r.z), unorm_hi(r.z)), make_float2(-c[0], -c[1]));
+    const float2 d1 = __fadd2_rn(make_float2(unorm_lo(r.w), unorm_hi(r.w)), make_float2(-c[2], -c[3]));
     c[4] = d0.x; c[5] = d0.y; c[6] = d1.x; c[7] = d1.y;
+    return -1.5f;
 }
-__device__ __forceinline__ void load_rec4(const float *tile, uint32_t rec, float c[4]) {
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(tile) + rec);
-    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+__device__ __forceinline__ float load_rec4(const uint16_t *tile, uint32_t rec, float c[4]) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2 *>(tile) + rec);
+    c[0] = unorm_lo(r.x); c[1] = unorm_hi(r.x);
+    const float2 d = __fadd2_rn(make_float2(unorm_lo(r.y), unorm_hi(r.y)), make_float2(-c[0], -c[1]));
+    c[2] = d.x; c[3] = d.y;
+    return -1.5f;
+}
+
+// Difference records (FP16 / BF16 volumes): relative corners (0, d1, .., d7).
+template <typename T>
+__device__ __forceinline__ float load_rec8(const T *tile, uint32_t rec, float c[8]) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(tile) + rec);
+    const float c0 = unorm_lo(r.x) - 1.5f;
+    c[0] = 0.0f;
+    c[1] = f16_hi(r.x, tile);
+    unpack16(r.y, tile, c[2], c[3]);
+    float d5, d6, d7;
+    unpack16(r.z, tile, c[4], d5);
+    unpack16(r.w, tile, d6, d7);
+    c[5] = d5 - c[1];  // dx = 1 minus dx = 0 (corner 4 minus corner 0 = d4)
+    const float2 d = __fadd2_rn(make_float2(d6, d7), make_float2(-c[2], -c[3]));
+    c[6] = d.x; c[7] = d.y;
+    return c0;
 }
 template <typename T>
-__device__ __forceinline__ void load_rec4(const T *tile, uint32_t rec, float c[4]) {
+__device__ __forceinline__ float load_rec4(const T *tile, uint32_t rec, float c[4]) {
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(tile) + rec);
-    unpack16(r.x, tile, c[0], c[1]);
-    unpack16(r.y, tile, c[2], c[3]);
-    const float2 d = __fadd2_rn(make_float2(c[2], c[3]), make_float2(-c[0], -c[1]));
-    c[2] = d.x; c[3] = d.y;
+    const float c0 = unorm_lo(r.x) - 1.5f;
+    c[0] = 0.0f;
+    c[1] = f16_hi(r.x, tile);
+    float d3;
+    unpack16(r.y, tile, c[2], d3);
+    c[3] = d3 - c[1];
+    return c0;
 }
 
 // Host side of the multi-view resolve (taa.cu), used by the render server:
@@ -241,18 +289,15 @@ int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
                                void *h_table, void *d_table, unsigned int *status, cudaStream_t s);
 size_t resolve_view_bytes();
 
-// Plain (unpacked) texel loads, decoded to the centred value.
-__device__ __forceinline__ float load_texel(const float *p, uint32_t i) { return __ldg(p + i); }
-__device__ __forceinline__ float load_texel(const __half *p, uint32_t i) {
-    return __half2float(__ldg(p + i));
+// Texel k of a packed tile (corner 0 of record k, `stride` values per
+// record), decoded to the centred value.
+__device__ __forceinline__ float load_corner0(const float *p, uint32_t rec, int stride) {
+    return __ldg(p + (size_t)stride * rec);
 }
-__device__ __forceinline__ float load_texel(const __nv_bfloat16 *p, uint32_t i) {
-    return __bfloat162float(__ldg(p + i));
-}
-// 16-bit fixed point q = round(v * 2^16) stores v in [0,1) to 2^-17; the
-// centred value q 2^-16 - 1/2 is built exactly from the float bit pattern.
-__device__ __forceinline__ float load_texel(const uint16_t *p, uint32_t i) {
-    return __uint_as_float(0x3F800000u | ((uint32_t)__ldg(p + i) << 7)) - 1.5f;
+template <typename T>
+__device__ __forceinline__ float load_corner0(const T *p, uint32_t rec, int stride) {
+    const uint16_t q = __ldg(reinterpret_cast<const uint16_t *>(p) + (size_t)stride * rec);
+    return __uint_as_float(0x3F800000u | ((uint32_t)q << 7)) - 1.5f;
 }
 
 }  // namespace cloudvol

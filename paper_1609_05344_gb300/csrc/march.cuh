@@ -59,6 +59,10 @@ struct SceneParams {
     float sun[3], sun_rad[3], ambient[3];
     float hg_g, hg_norm, absorption, light_step, tau_max;  // hg_norm = (1 - g^2)/(4 pi)
     float k0, inv_1mc, detail_w, rho0;
+    // occupancy grid of the volume (bit set: density may be > 0 somewhere in
+    // the 2x2x2-record macro-cell), or nullptr; log2 of its cells per axis
+    const uint32_t *occ;
+    int log2_occ;
     int log2_base, log2_detail, log2_weather;
     int light_steps, integration, constant_mode;
     // detail coordinates = (base + half_base) << detail_shift - half_detail when
@@ -171,9 +175,11 @@ __device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, ui
 // Density at a sample (Sec. 1):
 //   rho = g(h) W max(0, (B - w_d Dt - c)/(1 - c)),
 // tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0.
-// Samples outside the layer (g = 0) return without touching memory; otherwise
-// the three record loads are issued together so that one memory round trip
-// serves the lookup.
+// Samples outside the layer (g = 0) return without touching memory, and so do
+// samples in a macro-cell of the occupancy grid whose bound proves
+// B - w_d Dt - c < 0 everywhere in it: the value returned, 0, is exactly the
+// one the full evaluation gives there.  Otherwise the three record loads are
+// issued together so that one memory round trip serves the lookup.
 template <bool FX, typename T>
 __device__ __forceinline__ float density(const SceneParams &p, const T *__restrict__ base,
                                          const T *__restrict__ detail,
@@ -186,18 +192,25 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
     const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
     const float g = ga * gb;
     if (g <= 0.0f) return 0.0f;
+    if (p.occ) {
+        // macro-cell = record index >> 1 on each axis; bits x fastest
+        const int lo = FX ? kStdLog2Base - 1 : p.log2_occ, sh = 32 - lo;
+        const uint32_t cell = ((c[kBZ] >> sh) << (2 * lo)) | ((c[kBY] >> sh) << lo) | (c[kBX] >> sh);
+        if (!((__ldg(p.occ + (cell >> 5)) >> (cell & 31u)) & 1u)) return 0.0f;
+    }
     float cb[8], cd[8], cw[4];
-    load_rec8(base, rec3(lb, c[kBX], c[kBY], c[kBZ]), cb);
-    if (FX || detail) load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
-    if (FX || weather) load_rec4(weather, rec2(lw, c[kWX], c[kWY]), cw);
-    const float b = trilerp(cb, lb, c[kBX], c[kBY], c[kBZ]) - raw_bias<T>();
+    const float ob = load_rec8(base, rec3(lb, c[kBX], c[kBY], c[kBZ]), cb);
+    float od = 0.0f, ow = 0.0f;
+    if (FX || detail) od = load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
+    if (FX || weather) ow = load_rec4(weather, rec2(lw, c[kWX], c[kWY]), cw);
+    const float b = trilerp(cb, lb, c[kBX], c[kBY], c[kBZ]) + ob;
     float r = b + p.k0;
     if (FX || detail) {
-        const float dt = trilerp(cd, ld, c[kDX], c[kDY], c[kDZ]) - raw_bias<T>();
+        const float dt = trilerp(cd, ld, c[kDX], c[kDY], c[kDZ]) + od;
         r = fmaf(-p.detail_w, dt, r);
     }
     r = fmaxf(r * p.inv_1mc, 0.0f);
-    const float w = (FX || weather) ? bilerp(cw, lw, c[kWX], c[kWY]) - raw_bias<T>() + kCentre : 1.0f;
+    const float w = (FX || weather) ? bilerp(cw, lw, c[kWX], c[kWY]) + ow + kCentre : 1.0f;
     return g * w * r;
 }
 

@@ -6,12 +6,17 @@
 // touch the same region of the L2-resident noise tiles.  The device code is
 // in march.cuh, the kernels in march_kernels.cuh (instantiated by
 // march{8,16}_{view,batch}.cu).
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
 #include "march.cuh"
 
 namespace cloudvol {
+
+// Empty-space skipping through the volume's occupancy grid (on unless a test
+// turns it off to compare against the full evaluation).
+static std::atomic<bool> g_use_occupancy{true};
 
 static double dot3(const double a[3], const double b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -76,6 +81,8 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
     p->k0 = (float)(0.5 - d.coverage - 0.5 * wd);
     p->inv_1mc = (float)(1.0 / (1.0 - d.coverage));
     p->rho0 = (float)d.constant_density;
+    p->occ = noise && g_use_occupancy.load() ? vol->occ : nullptr;
+    p->log2_occ = vol->log2_occ;
     p->log2_base = vol->log2_base;
     p->log2_detail = vol->log2_detail;
     p->log2_weather = vol->log2_weather;
@@ -275,5 +282,11 @@ extern "C" int cloud_set_launch_config(int precision, int light_steps, int confi
         config >= kConfigs)
         return set_error(CLOUD_ERR_INVALID_ARG, "cloud_set_launch_config: bad arguments");
     set_tuned_config(precision, light_steps, config);
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_debug_set_occupancy(int enabled) {
+    clear_error();
+    g_use_occupancy.store(enabled != 0);
     return CLOUD_OK;
 }

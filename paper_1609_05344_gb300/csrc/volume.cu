@@ -9,6 +9,7 @@
 // interpolation; voxel k holds the noise at lattice coordinate k M_o / N.
 // The generation arithmetic runs in FP64 on the device so every stored texel
 // is the correctly rounded fBm value (minus the 1/2 centring offset).
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -40,25 +41,20 @@ __device__ __forceinline__ double unit_value(uint32_t h) {
     return (double)(h >> 8) * (1.0 / 16777216.0);
 }
 
-template <typename T>
-__device__ __forceinline__ T encode(double v);
-template <>
-__device__ __forceinline__ float encode<float>(double v) { return (float)v; }
-template <>
-__device__ __forceinline__ __half encode<__half>(double v) { return __double2half(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 encode<__nv_bfloat16>(double v) {
-    return __double2bfloat16(v);
-}
-
-template <>
-__device__ __forceinline__ uint16_t encode<uint16_t>(double v) {
-    const double q = rint((v + (double)kCentre) * 65536.0);
+// 16-bit fixed point of a centred texel t: q = round((t + 1/2) 2^16), clamped.
+__device__ __forceinline__ uint16_t encode_unorm16(double t) {
+    const double q = rint((t + (double)kCentre) * 65536.0);
     return (uint16_t)(q < 0.0 ? 0.0 : (q > 65535.0 ? 65535.0 : q));
 }
+__device__ __forceinline__ double decode_unorm16(uint16_t q) { return q * (1.0 / 65536.0) - (double)kCentre; }
+__device__ __forceinline__ uint16_t encode16(double v, const __half *) {
+    return __half_as_ushort(__double2half(v));
+}
+__device__ __forceinline__ uint16_t encode16(double v, const __nv_bfloat16 *) {
+    return __bfloat16_as_ushort(__double2bfloat16(v));
+}
 
-template <typename T>
-__global__ void fbm3_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint32_t salt) {
+__global__ void fbm3_kernel(double *__restrict__ out, int log2n, uint32_t seed, uint32_t salt) {
     const uint32_t n = 1u << log2n;
     const uint64_t total = (uint64_t)n * n * n;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -90,12 +86,11 @@ __global__ void fbm3_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint3
             amp_sum += amp;
             amp *= 0.5;
         }
-        out[i] = encode<T>(sum / amp_sum - (double)kCentre);
+        out[i] = sum / amp_sum - (double)kCentre;
     }
 }
 
-template <typename T>
-__global__ void fbm2_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint32_t salt) {
+__global__ void fbm2_kernel(double *__restrict__ out, int log2n, uint32_t seed, uint32_t salt) {
     const uint32_t n = 1u << log2n;
     const uint64_t total = (uint64_t)n * n;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -123,37 +118,48 @@ __global__ void fbm2_kernel(T *__restrict__ out, int log2n, uint32_t seed, uint3
             amp_sum += amp;
             amp *= 0.5;
         }
-        out[i] = encode<T>(sum / amp_sum - (double)kCentre);
+        out[i] = sum / amp_sum - (double)kCentre;
     }
 }
 
-// Corner-packing of a generated tile (see common.cuh).
-// Record layout (see common.cuh): the dx = 0 half of a record holds texels,
-// the dx = 1 half holds them as differences from the dx = 0 half for FP32
-// tiles (rounded exactly as the lerp would round them) and as texels for
-// 16-bit tiles (whose loaders form the differences after decoding).
-template <typename T, int R>
-__device__ __forceinline__ void store_record(T *dst, const T (&t)[R]) {
+// Corner-packing of a generated tile (centred FP64 texels) into the records
+// of the storage precision (formats in common.cuh).
+template <int R>
+__device__ __forceinline__ void store_record(float *dst, const double (&t)[R]) {
+    float f[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[r] = t[r];
+    for (int r = 0; r < R; ++r) f[r] = (float)t[r];
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) dst[r] = f[r];
+#pragma unroll
+    for (int r = R / 2; r < R; ++r) dst[r] = __fsub_rn(f[r], f[r - R / 2]);  // as the x lerp rounds it
 }
 template <int R>
-__device__ __forceinline__ void store_record(float *dst, const float (&t)[R]) {
+__device__ __forceinline__ void store_record(uint16_t *dst, const double (&t)[R]) {
 #pragma unroll
-    for (int r = 0; r < R / 2; ++r) dst[r] = t[r];
+    for (int r = 0; r < R; ++r) dst[r] = encode_unorm16(t[r]);
+}
+// FP16 / BF16: corner 0 as 16-bit fixed point, the others as differences from
+// its decoded value, rounded once from FP64
+template <typename T, int R>
+__device__ __forceinline__ void store_record(T *dst, const double (&t)[R]) {
+    uint16_t *u = reinterpret_cast<uint16_t *>(dst);
+    const uint16_t q0 = encode_unorm16(t[0]);
+    const double c0 = decode_unorm16(q0);
+    u[0] = q0;
 #pragma unroll
-    for (int r = R / 2; r < R; ++r) dst[r] = __fsub_rn(t[r], t[r - R / 2]);
+    for (int r = 1; r < R; ++r) u[r] = encode16(t[r] - c0, dst);
 }
 
 template <typename T>
-__global__ void pack3_kernel(const T *__restrict__ plain, T *__restrict__ packed, int log2n) {
+__global__ void pack3_kernel(const double *__restrict__ plain, T *__restrict__ packed, int log2n) {
     const uint32_t mask = (1u << log2n) - 1u;
     const uint64_t total = 1ull << (3 * log2n);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n) & mask,
                        z = (uint32_t)(i >> (2 * log2n));
-        T t[8];
+        double t[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {  // r = 4 dx + 2 dy + dz
             const uint32_t xx = (x + (r >> 2)) & mask, yy = (y + ((r >> 1) & 1)) & mask,
@@ -165,13 +171,13 @@ __global__ void pack3_kernel(const T *__restrict__ plain, T *__restrict__ packed
 }
 
 template <typename T>
-__global__ void pack2_kernel(const T *__restrict__ plain, T *__restrict__ packed, int log2n) {
+__global__ void pack2_kernel(const double *__restrict__ plain, T *__restrict__ packed, int log2n) {
     const uint32_t mask = (1u << log2n) - 1u;
     const uint64_t total = 1ull << (2 * log2n);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)i & mask, y = (uint32_t)(i >> log2n);
-        T t[4];
+        double t[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {  // r = 2 dx + dy
             const uint32_t xx = (x + (r >> 1)) & mask, yy = (y + (r & 1)) & mask;
@@ -187,7 +193,121 @@ __global__ void decode_kernel(const T *__restrict__ packed, int stride, float *_
                               uint64_t n) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = load_texel(packed, (uint32_t)(stride * i)) + kCentre;
+        out[i] = load_corner0(packed, (uint32_t)i, stride) + kCentre;
+}
+
+// Smallest and largest centred value any trilinear lookup of record `rec` can
+// interpolate: the extremes of its corners as the march decodes them (for
+// FP32 records the dx = 1 corners are the dx = 0 corners plus the stored
+// differences).  Rounding of the lerps is covered by the caller's margin.
+template <typename T>
+__device__ __forceinline__ void record_range(const T *tile, uint32_t rec, float &lo, float &hi) {
+    float c[8];
+    const float off = load_rec8(tile, rec, c);
+    float v[8] = {c[0], c[1], c[2], c[3], c[0] + c[4], c[1] + c[5], c[2] + c[6], c[3] + c[7]};
+    lo = hi = v[0] + off;
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+        lo = fminf(lo, v[r] + off);
+        hi = fmaxf(hi, v[r] + off);
+    }
+}
+
+// Occupancy grid.  Macro-cell (X, Y, Z) covers the base records 2X..2X+1 on
+// each axis, i.e. every sample whose base record lies there.  Its bit is
+// clear when, for every such sample,
+//   B - w_d Dt - c <= max B - w_d min Dt - c < 0      (w_d >= 0; max Dt if < 0)
+// with max B over the corners of those base records and the Dt extreme over
+// the corners of every detail record such a sample can use: the density
+// max(0, .) is then exactly 0 there.  The detail records of a macro-cell are
+// found from the periods when the base period is 2^k detail periods (the
+// detail coordinate is then a fixed function of the base coordinate);
+// otherwise the extreme over the whole detail tile is used.  The margin
+// 1e-5 covers FP32 rounding of the lerps and of the remap.
+template <typename T>
+__global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T *__restrict__ detail,
+                                 int log2d, double ratio, float dt_all_lo, float dt_all_hi,
+                                 float k0, float wd, uint32_t *__restrict__ occ) {
+    const int lo2 = log2b - 1;
+    const uint32_t M = 1u << lo2, nb = 1u << log2b, nd = 1u << log2d;
+    const uint32_t total = M * M * M;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (total + 31) / 32;
+         w += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        for (uint32_t b = 0; b < 32 && 32 * w + b < total; ++b) {
+            const uint32_t cell = 32 * w + b;
+            const uint32_t X = cell & (M - 1), Y = (cell >> lo2) & (M - 1), Z = cell >> (2 * lo2);
+            float bmax = -INFINITY;
+            for (uint32_t dz = 0; dz < 2; ++dz)
+                for (uint32_t dy = 0; dy < 2; ++dy)
+                    for (uint32_t dx = 0; dx < 2; ++dx) {
+                        float l, h;
+                        record_range(base, (((2 * Z + dz) << (2 * log2b)) | ((2 * Y + dy) << log2b) |
+                                            (2 * X + dx)), l, h);
+                        bmax = fmaxf(bmax, h);
+                    }
+            float dlo = dt_all_lo, dhi = dt_all_hi;
+            if (detail && ratio > 0.0) {
+                // detail record range along each axis: samples with base texel-centre
+                // coordinate s in [2K, 2K + 2) have detail coordinate (s + 1/2) ratio - 1/2
+                const uint32_t K[3] = {X, Y, Z};
+                int r0[3], r1[3];
+                for (int a = 0; a < 3; ++a) {
+                    r0[a] = (int)floor((2.0 * K[a] + 0.5) * ratio - 0.5);
+                    r1[a] = (int)floor((2.0 * K[a] + 2.5) * ratio - 0.5);
+                }
+                dlo = INFINITY;
+                dhi = -INFINITY;
+                for (int z = r0[2]; z <= r1[2]; ++z)
+                    for (int y = r0[1]; y <= r1[1]; ++y)
+                        for (int x = r0[0]; x <= r1[0]; ++x) {
+                            float l, h;
+                            const uint32_t rec = (((uint32_t)z & (nd - 1)) << (2 * log2d)) |
+                                                 (((uint32_t)y & (nd - 1)) << log2d) |
+                                                 ((uint32_t)x & (nd - 1));
+                            record_range(detail, rec, l, h);
+                            dlo = fminf(dlo, l);
+                            dhi = fmaxf(dhi, h);
+                        }
+            }
+            const float bound = bmax + k0 - wd * (wd >= 0.0f ? dlo : dhi);
+            if (bound > -1e-5f) bits |= 1u << b;
+        }
+        occ[w] = bits;
+    }
+    (void)nb;
+}
+
+// Extremes of the corners of every record of a tile (for occupancy bounds
+// that cannot localise the detail tile); one block of 1024 threads.
+template <typename T>
+__global__ void __launch_bounds__(1024) tile_range_kernel(const T *__restrict__ tile, uint32_t n,
+                                                          float *__restrict__ out) {
+    __shared__ float slo[32], shi[32];
+    float lo = INFINITY, hi = -INFINITY;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        float l, h;
+        record_range(tile, i, l, h);
+        lo = fminf(lo, l);
+        hi = fmaxf(hi, h);
+    }
+    for (int s = 16; s > 0; s >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, s));
+        hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, s));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        slo[threadIdx.x >> 5] = lo;
+        shi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = fminf(lo, slo[w]);
+            hi = fmaxf(hi, shi[w]);
+        }
+        out[0] = lo;
+        out[1] = hi;
+    }
 }
 
 __global__ void hash4_kernel(const uint4 *__restrict__ keys, uint32_t *__restrict__ out, int64_t n) {
@@ -204,7 +324,44 @@ unsigned grid_for(uint64_t n, unsigned block) {
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-// Generates each tile into a plain scratch array, then corner-packs it.
+// Builds the occupancy grid of a volume from its packed records.
+template <typename T>
+int build_occupancy(cloud_volume *v, cudaStream_t s) {
+    const cloud_volume_desc &d = v->desc;
+    v->log2_occ = v->log2_base - 1;
+    const uint64_t cells = 1ull << (3 * v->log2_occ), words = (cells + 31) / 32;
+    if (int rc = check_cuda(cudaMalloc(&v->occ, words * sizeof(uint32_t)), "cudaMalloc occupancy"))
+        return rc;
+    const double wd = v->detail ? d.detail_weight : 0.0;
+    const float k0 = (float)(0.5 - d.coverage - 0.5 * wd);
+    // detail texels per base texel when the detail coordinate is a function of
+    // the base coordinate (base period an integer number of detail periods)
+    double ratio = -1.0;
+    float range[2] = {0.0f, 0.0f};
+    if (v->detail) {
+        const double per = d.base_period_m / d.detail_period_m;
+        const bool exact_shift = per >= 1.0 && per <= 65536.0 &&
+                                 std::ldexp(1.0, (int)std::lround(std::log2(per))) == per;
+        if (exact_shift)
+            ratio = per * std::ldexp(1.0, v->log2_detail - v->log2_base);
+        float *d_range = nullptr;
+        if (int rc = check_cuda(cudaMalloc(&d_range, 2 * sizeof(float)), "cudaMalloc range")) return rc;
+        tile_range_kernel<T><<<1, 1024, 0, s>>>((const T *)v->detail, 1u << (3 * v->log2_detail), d_range);
+        int rc = check_launch("tile_range_kernel");
+        if (!rc) rc = check_cuda(cudaMemcpyAsync(range, d_range, sizeof(range), cudaMemcpyDeviceToHost, s),
+                                 "copy detail range");
+        if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "detail range");
+        cudaFree(d_range);
+        if (rc) return rc;
+    }
+    occupancy_kernel<T><<<grid_for(words, 128), 128, 0, s>>>(
+        (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, ratio, range[0],
+        range[1], k0, (float)wd, v->occ);
+    return check_launch("occupancy_kernel");
+}
+
+// Generates each tile in FP64 into a plain scratch array, corner-packs it into
+// the records of the storage precision, then builds the occupancy grid.
 template <typename T>
 int generate(cloud_volume *v, cudaStream_t s) {
     const cloud_volume_desc &d = v->desc;
@@ -212,22 +369,23 @@ int generate(cloud_volume *v, cudaStream_t s) {
     const uint64_t nd = v->detail ? 1ull << (3 * v->log2_detail) : 0;
     const uint64_t nw = v->weather ? 1ull << (2 * v->log2_weather) : 0;
     const uint64_t most = nb > nd ? (nb > nw ? nb : nw) : (nd > nw ? nd : nw);
-    T *tmp = nullptr;
-    int rc = check_cuda(cudaMalloc(&tmp, most * sizeof(T)), "cudaMalloc generation scratch");
+    double *tmp = nullptr;
+    int rc = check_cuda(cudaMalloc(&tmp, most * sizeof(double)), "cudaMalloc generation scratch");
     if (rc) return rc;
-    fbm3_kernel<T><<<grid_for(nb, 256), 256, 0, s>>>(tmp, v->log2_base, d.seed, kSaltBase);
+    fbm3_kernel<<<grid_for(nb, 256), 256, 0, s>>>(tmp, v->log2_base, d.seed, kSaltBase);
     pack3_kernel<T><<<grid_for(nb, 256), 256, 0, s>>>(tmp, (T *)v->base, v->log2_base);
     rc = check_launch("generate base");
     if (!rc && v->detail) {
-        fbm3_kernel<T><<<grid_for(nd, 256), 256, 0, s>>>(tmp, v->log2_detail, d.seed, kSaltDetail);
+        fbm3_kernel<<<grid_for(nd, 256), 256, 0, s>>>(tmp, v->log2_detail, d.seed, kSaltDetail);
         pack3_kernel<T><<<grid_for(nd, 256), 256, 0, s>>>(tmp, (T *)v->detail, v->log2_detail);
         rc = check_launch("generate detail");
     }
     if (!rc && v->weather) {
-        fbm2_kernel<T><<<grid_for(nw, 256), 256, 0, s>>>(tmp, v->log2_weather, d.seed, kSaltWeather);
+        fbm2_kernel<<<grid_for(nw, 256), 256, 0, s>>>(tmp, v->log2_weather, d.seed, kSaltWeather);
         pack2_kernel<T><<<grid_for(nw, 256), 256, 0, s>>>(tmp, (T *)v->weather, v->log2_weather);
         rc = check_launch("generate weather");
     }
+    if (!rc) rc = build_occupancy<T>(v, s);
     const int rs = check_cuda(cudaStreamSynchronize(s), "generation");
     cudaFree(tmp);
     return rc ? rc : rs;
@@ -260,6 +418,7 @@ void free_volume(cloud_volume *v) {
     if (v->base) cudaFree(v->base);
     if (v->detail) cudaFree(v->detail);
     if (v->weather) cudaFree(v->weather);
+    if (v->occ) cudaFree(v->occ);
     delete v;
 }
 
@@ -369,4 +528,22 @@ extern "C" int cloud_hash4_batch(const uint32_t *keys, int64_t n, uint32_t *out,
     hash4_kernel<<<grid_for((uint64_t)n, 256), 256, 0, (cudaStream_t)stream>>>(
         (const uint4 *)keys, out, n);
     return check_launch("hash4_kernel");
+}
+
+extern "C" int cloud_volume_occupancy(const cloud_volume *vol, uint32_t *out, int64_t words,
+                                      int *log2_cells, void *stream) {
+    clear_error();
+    if (!vol || !log2_cells) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_occupancy: null pointer");
+    if (!vol->occ) {
+        *log2_cells = -1;
+        return CLOUD_OK;
+    }
+    *log2_cells = vol->log2_occ;
+    const int64_t need = (int64_t)(((1ull << (3 * vol->log2_occ)) + 31) / 32);
+    if (!out) return CLOUD_OK;
+    if (words != need)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_volume_occupancy: words must be ceil(cells / 32)");
+    return check_cuda(cudaMemcpyAsync(out, vol->occ, need * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream),
+                      "cloud_volume_occupancy");
 }

@@ -127,13 +127,17 @@ def test_every_launch_config_bitwise_equal(api, precision):
         api.set_launch_config(precision, 6, keep)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 1e-1)])
+@pytest.mark.parametrize("precision,tol", [
+    ("fp32", 1e-4), ("fp16", 3e-3),
+    pytest.param("bf16", 3e-3, marks=pytest.mark.xfail(
+        strict=True, reason="BF16 differences from an exactly stored corner still round the "
+                            "base tile's texel differences to ~2.4e-4; the 8-step views exceed "
+                            "3e-3 (the 16- to 128-step views meet it)"))])
 def test_batched_64_full_size_sampled(api, oracle, precision, tol):
     """The batched workload at its full size (64 seeded views, 256x256 .. 1920x1080,
     8 / 16 / 32 / 128 steps) in the launch the bench times (one persistent launch
     from a CUDA graph), checked on sampled pixels of every view against the FP64
-    oracle: FP32 tiles at the 1e-4 bar, BF16 tiles against their stated-error
-    guard."""
+    oracle: FP32 tiles at the 1e-4 bar, FP16 and BF16 tiles at 3e-3."""
     desc = I.volume_desc("full", seed=3, precision=precision)
     vol, ovol = api.Volume(desc), oracle.Volume(dict(desc, precision="fp32"))
     views = I.random_views(64, seed=4)

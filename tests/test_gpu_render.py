@@ -41,7 +41,7 @@ def test_hash_bitwise(api, oracle):
     assert np.array_equal(got, oracle.hash4_batch(keys))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-7), ("fp16", 2.5e-4), ("bf16", 2e-3),
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-7), ("fp16", 7.7e-6), ("bf16", 7.7e-6),
                                            ("unorm16", 7.7e-6)])
 def test_volume_generation(api, oracle, precision, tol):
     desc = I.volume_desc("full", seed=2, precision=precision, base_n=64)
@@ -125,16 +125,85 @@ def test_fast_1080p_unorm16_volumes(api, oracle, frame):
     assert err <= TOL_FP16
 
 
-@pytest.mark.parametrize("precision,guard", [("fp16", 1e-2), ("bf16", 1e-1)])
-def test_fast_1080p_float16_volumes_stated_error(api, oracle, precision, guard):
-    # 8 steps of up to 3.5 km amplify storage error (FP16 2^-12, BF16 2^-9 per
-    # centred texel) by alpha*D*L_in ~ 270: the error is stated, with a guard
+@pytest.mark.parametrize("frame", [3, 11])
+def test_fast_1080p_fp16_volumes(api, oracle, frame):
+    # FP16 records (corner 0 as 16-bit fixed point, the other corners as half
+    # differences from it) meet the reduced-precision tolerance on the 8-step
+    # fast path at half the record bytes of FP32
     wl = I.workload("fast-1080p")
-    err, _ = _sampled(api, oracle, wl, I.orbit_camera(3, 3), 3, 40000, 5, precision=precision)
-    print(f"fast-1080p {precision} volumes: max abs err {err:.3e}")
-    assert err <= guard
+    err, _ = _sampled(api, oracle, wl, I.orbit_camera(frame, 3), frame, 40000, 5 + frame,
+                      precision="fp16")
+    print(f"fast-1080p fp16 volumes frame {frame}: max abs err {err:.3e}")
+    assert err <= TOL_FP16
 
 
+@pytest.mark.xfail(strict=True, reason="BF16 keeps 8 significant bits: even as differences from "
+                                       "an exactly stored corner, the base tile's texel "
+                                       "differences (up to ~0.13) round to ~2.4e-4, which 8 view "
+                                       "steps of up to 3.5 km amplify past 3e-3")
+def test_fast_1080p_bf16_volumes(api, oracle):
+    wl = I.workload("fast-1080p")
+    err, _ = _sampled(api, oracle, wl, I.orbit_camera(3, 3), 3, 40000, 5, precision="bf16")
+    print(f"fast-1080p bf16 volumes: max abs err {err:.3e}")
+    assert err <= TOL_FP16
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "unorm16"])
+@pytest.mark.parametrize("frame", [3, 20])
+def test_occupancy_skip_is_bitwise_exact(api, frame, precision):
+    """Skipping the memory reads of lookups in macro-cells the occupancy grid
+    proves empty changes no pixel: a full-size fast-1080p frame is bitwise the
+    same with the grid in use and with every lookup evaluated."""
+    import torch
+    wl = I.workload("fast-1080p", precision=precision)
+    vol = api.Volume(wl.volume)
+    cam = I.orbit_camera(frame, 3)
+    try:
+        api.set_occupancy(False)
+        full, n_full = api.render(vol, cam, I.params(), wl.width, wl.height, wl.steps,
+                                  wl.light_steps, jitter_frame=frame, count=True)
+        api.set_occupancy(True)
+        skip, n_skip = api.render(vol, cam, I.params(), wl.width, wl.height, wl.steps,
+                                  wl.light_steps, jitter_frame=frame, count=True)
+    finally:
+        api.set_occupancy(True)
+    assert torch.equal(full, skip)
+    assert int(n_full.item()) == int(n_skip.item())  # the same lookups, fewer of them read memory
+
+
+def test_occupancy_grid_is_conservative(api, oracle):
+    """Every macro-cell the grid marks empty really has no density: checked on
+    the FP64 oracle texels (max B - w_d min Dt - c < 0 over the base and detail
+    texels any sample of the cell interpolates), and the grid marks a
+    substantial share of the cells empty."""
+    desc = I.volume_desc("full", seed=3)
+    occ = api.Volume(desc).occupancy()
+    ov = oracle.Volume(desc)
+    B, Dt = ov.base, ov.detail
+    nb, nd = B.shape[0], Dt.shape[0]
+    assert occ.shape == (nb // 2,) * 3
+    Bp = np.pad(B, ((0, 2), (0, 2), (0, 2)), mode="wrap")
+    bmax = np.full(occ.shape, -np.inf)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                bmax = np.maximum(bmax, Bp[dz:dz + nb:2, dy:dy + nb:2, dx:dx + nb:2])
+    # detail texels of base macro-cell K (base texels 2K..2K+2 at 2 detail texels each,
+    # base period = 8 detail periods): detail texels 4K .. 4K+5 (mod nd)
+    ratio = desc["base_period"] / desc["detail_period"] * nd / nb
+    assert ratio == 2.0
+    Dp = np.pad(Dt, ((0, 6), (0, 6), (0, 6)), mode="wrap")
+    dmin = np.full((nd // 4,) * 3, np.inf)
+    for dz in range(6):
+        for dy in range(6):
+            for dx in range(6):
+                dmin = np.minimum(dmin, Dp[dz:dz + nd:4, dy:dy + nd:4, dx:dx + nd:4])
+    k = np.arange(nb // 2) % (nd // 4)
+    dmin_cells = dmin[np.ix_(k, k, k)]
+    bound = bmax - desc["detail_weight"] * dmin_cells - desc["coverage"]
+    empty = ~occ
+    assert empty.mean() > 0.2
+    assert bound[empty].max() < 0.0
 def test_reference_720p_sampled(api, oracle):
     wl = I.workload("reference")
     err, _ = _sampled(api, oracle, wl, I.ground_camera(), -1, 4000, 9)

@@ -184,7 +184,7 @@ def test_served_full_size_fp16(api, oracle):
     """The served configuration at its largest session (1920x1080, FP16 tiles
     and FP16 history) next to a small one in the same batches: three frames of
     each against the FP64 oracle chain (render -> motion -> TAA), within the
-    FP16 stated-error guard; the small session is also bitwise the same alone."""
+    reduced-precision tolerance 3e-3."""
     desc = I.volume_desc("full", seed=3, precision="fp16")
     vol, ovol = api.Volume(desc), oracle.Volume(dict(desc, precision="fp32"))
     prm = I.params()
@@ -206,7 +206,7 @@ def test_served_full_size_fp16(api, oracle):
             worst = max(worst, float(np.abs(srv.output(sids[k]).astype(np.float64) - ohist[k]).max()))
     srv.close()
     print(f"served fp16 full size: max abs err {worst:.3e}")
-    assert worst <= 5e-2
+    assert worst <= 3e-3
 
 
 def test_served_frames_equal_session_frames(api):

@@ -75,9 +75,10 @@ def test_taa_rejects_overlap(api):
 
 
 # FP16 history: each resolve rounds to 2^-11 relative (values <= 2) and the
-# blend carries 0.9 of it forward, so the chain error is bounded by
-# 2^-11 * 2 / 0.1 ~ 1e-2 (plus the render tolerance).
-@pytest.mark.parametrize("fmt,tol", [("fp32", 1e-4), ("fp16", 1e-2)])
+# blend carries 0.9 of it forward, so after 8 frames the chain error is at
+# most 2^-11 (values below 2) times sum_{k<8} 0.9^k = 5.7, i.e. 2.8e-3, plus
+# the render tolerance: within the reduced-precision tolerance 3e-3.
+@pytest.mark.parametrize("fmt,tol", [("fp32", 1e-4), ("fp16", 3e-3)])
 def test_session_matches_oracle_chain(api, oracle, fmt, tol):
     import torch
     desc = I.volume_desc("full", seed=3)
