@@ -74,10 +74,10 @@ def test_taa_rejects_overlap(api):
         api.taa(buf, buf, mot, out=buf)
 
 
-# FP16 history: each resolve rounds to 2^-11 relative (values <= 2) and the
-# blend carries 0.9 of it forward, so after 8 frames the chain error is at
-# most 2^-11 (values below 2) times sum_{k<8} 0.9^k = 5.7, i.e. 2.8e-3, plus
-# the render tolerance: within the reduced-precision tolerance 3e-3.
+# FP16 history: each resolve rounds its output by at most 2^-11 (values below
+# 2) and the blend carries 0.9 of that forward, so after 8 frames the chain
+# error is at most 2^-11 sum_{k<8} 0.9^k = 2^-11 * 5.7 = 2.8e-3, plus the
+# render tolerance: within the reduced-precision tolerance 3e-3.
 @pytest.mark.parametrize("fmt,tol", [("fp32", 1e-4), ("fp16", 3e-3)])
 def test_session_matches_oracle_chain(api, oracle, fmt, tol):
     import torch
