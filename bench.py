@@ -232,7 +232,10 @@ def cpu_baseline(wl, prm, budget_s=12.0, gpu_frame=None):
 
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores (there is no
-    published implementation of the paper to run)."""
+    published implementation of the paper to run), timed over whole frames of
+    the workload: each step renders one 1920x1080 frame (row-parallel over the
+    host cores), computes its motion from the previous camera and resolves it
+    into the history, exactly the work of one GPU step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -243,22 +246,22 @@ def run_reference(args):
     prm = I.params()
     cores = os.cpu_count() or 1
     ovol = O.Volume(wl.volume)
-    band = max(1, wl.height // 16)  # a bounded sample: one 1920x67 band of each frame
-    rows = np.arange(band)
-    xs = np.tile(np.arange(wl.width), band)
-    times = []
+    seed = wl.volume["seed"]
+    hist, times = None, []
+    t_run = time.perf_counter()
     for f in range(args.warmup + args.steps):
-        cam = I.orbit_camera(f, wl.volume["seed"])
-        y0 = (f * band) % (wl.height - band + 1)
-        ys = np.repeat(rows + y0, wl.width)
+        cam = I.orbit_camera(f % wl.frames, seed)
         t0 = time.perf_counter()
-        O.render_pixels(ovol, cam, prm, wl.width, wl.height, wl.steps, wl.light_steps, xs, ys,
-                        jitter_frame=f, nthreads=cores)
+        img, _ = O.render(ovol, cam, prm, wl.width, wl.height, wl.steps, wl.light_steps,
+                          jitter_frame=f, nthreads=cores)
+        mot = (O.motion(wl.volume, prm, I.orbit_camera((f - 1) % wl.frames, seed), cam, wl.width,
+                        wl.height) if hist is not None else np.zeros((wl.height, wl.width, 2)))
+        hist = O.taa(hist, img, mot, blend=0.1)
         dt = time.perf_counter() - t0
         if f >= args.warmup:
             times.append(dt)
-    per_px = statistics.mean(times) / (band * wl.width)
-    frame_s = per_px * wl.width * wl.height
+    t_run = time.perf_counter() - t_run
+    frame_s = statistics.mean(times)
     value = wl.width * wl.height * wl.steps * (1 + wl.light_steps) / frame_s / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3,
@@ -268,11 +271,12 @@ def run_reference(args):
                        "steps": wl.steps, "light_steps": wl.light_steps, "jitter": "pixel",
                        "taa": True, "blend": 0.1, "volume_precision": "fp64 (the oracle's own)",
                        "volumes": "128^3 base + 32^3 detail + 512^2 weather",
-                       "sample": "the raymarch dominates the oracle's frame; motion and the "
-                                 "resolve are not in the band sample"},
+                       "frames": "32-frame seeded orbit"},
+            "frame_ms_p10_p50_p90": [float(np.percentile(times, q)) * 1e3 for q in (10, 50, 90)],
+            "wall_s": t_run,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"render of one {wl.width}x{band} band per step, FP64, "
-                                       f"{cores} threads, scaled to a frame"},
+                             "sample": f"{args.steps} whole frames (render + motion + TAA), FP64, "
+                                       f"render on {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -482,6 +486,22 @@ def run_gpu(args):
         "device_wait_timeouts": api.device_wait_timeouts(),
         "clocks": dict(clk.summary(), window="warm-up and timed frames"),
     }
+    if not args.no_extra_workloads:
+        # the other two configurations' headline comparisons, measured in the
+        # same run (BF16 tiles for the 64-view batch, FP16 tiles and history for
+        # serving, as the configurations state), each with its error vs FP64
+        bvol = api.Volume(I.volume_desc("full", seed=3, precision="bf16"))
+        line["batched_64"] = dict(
+            batched_measure(bvol, I.random_views(64, seed=4 + 1000 * rank), I.params(), 3, 3,
+                            local, oracle_pixels=8 if rank == 0 else 0),
+            volume_precision="bf16", views=64, steps="{8,16,32,128}",
+            sizes="256x256..1920x1080 seeded", timed_steps=3)
+        bvol.close()
+        svol = api.Volume(I.volume_desc("full", seed=3, precision="fp16"))
+        line["served"] = dict(served_measure(svol, I.params(), 500, 75, rank,
+                                             oracle_frames=3 if rank == 0 else 0),
+                              volume_precision="fp16", history="fp16")
+        svol.close()
     if world == 1 and not args.no_cpu_baseline:
         gpu0 = api.render(vol, I.orbit_camera(0, wl.volume["seed"]), prm, W, H, S, LS,
                           jitter_frame=0).cpu().numpy()
@@ -493,6 +513,73 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def batched_measure(vol, views, prm, steps, warmup, local, oracle_pixels=0):
+    """Config 4 (64 uneven views): one persistent launch replayed from a CUDA
+    graph, the same launch without the graph, and one launch per view, each
+    timed over `steps` steps with the L2 flushed between them; optionally the
+    max-abs error of the graph launch against the FP64 oracle on
+    `oracle_pixels` sampled pixels per view."""
+    import numpy as np
+    import torch
+
+    from paper_1609_05344_gb300 import _native, api
+    batch = api.Batch(vol, prm, views)
+    best, times = batch.autotune(repeats=2)
+    flush = L2Flush()
+    stream = torch.cuda.current_stream()
+
+    def launch(mode):
+        if mode == "graph":
+            batch.render(graph=True)
+        elif mode == "persistent":
+            batch.render()
+        else:
+            batch.render_per_view()
+
+    res = {}
+    for mode in ("graph", "persistent", "per_view"):
+        for k in range(warmup):
+            batch.set_views([dict(v, jitter_frame=k) for v in views])
+            launch(mode)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            flush(k)
+            batch.set_views([dict(v, jitter_frame=warmup + k) for v in views])
+            evs[k][0].record(stream)
+            launch(mode)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        res[mode] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    samples = sum(v["width"] * v["height"] * v["steps"] * 7 for v in views)
+    out = {"ms_graph": res["graph"], "ms_persistent_no_graph": res["persistent"],
+           "ms_one_launch_per_view": res["per_view"],
+           "speedup_vs_per_view": res["per_view"] / res["graph"],
+           "gsamples_s": samples / (res["graph"] * 1e-3) / 1e9, "launch_config": best,
+           "tile_shape_and_steps_per_iteration": list(_native.config_parts(best)),
+           "config_ms": times}
+    if oracle_pixels:
+        from oracle import oracle as O
+        batch.set_views(views)
+        outs = batch.render(graph=True)
+        ovol = O.Volume(dict(vol.desc, precision="fp32"))
+        rng = np.random.default_rng(9)
+        worst = 0.0
+        for v, o in zip(views, outs):
+            xs = rng.integers(0, v["width"], oracle_pixels)
+            ys = rng.integers(0, v["height"], oracle_pixels)
+            ref, _ = O.render_pixels(ovol, v["camera"], prm, v["width"], v["height"], v["steps"], 6,
+                                     xs, ys, jitter_frame=v["jitter_frame"],
+                                     nthreads=os.cpu_count() or 1)
+            worst = max(worst, float(np.abs(o.cpu().numpy()[ys, xs] - ref).max()))
+        ovol.close()
+        out["max_abs_err_vs_fp64"] = worst
+        out["err_sample"] = f"{oracle_pixels} seeded pixels of each view"
+    batch.close()
+    return out
 
 
 def run_batched(args):
@@ -510,89 +597,46 @@ def run_batched(args):
     vol = api.Volume(I.volume_desc("full", seed=3, precision=prec))
     prm = I.params()
     views = I.random_views(64, seed=4 + 1000 * rank)
-    samples = sum(v["width"] * v["height"] * v["steps"] * 7 for v in views)
     pixels = sum(v["width"] * v["height"] for v in views)
-    batch = api.Batch(vol, prm, views)
-    best, times = batch.autotune(repeats=2)
-    flush = L2Flush()
-    stream = torch.cuda.current_stream()
-
-    def step(k, mode):
-        batch.set_views([dict(v, jitter_frame=k) for v in views])
-        if mode == "graph":
-            batch.render(graph=True)
-        elif mode == "persistent":
-            batch.render()
-        else:
-            batch.render_per_view()
-
-    res = {}
     clk = ClockSampler(local).__enter__()
-    for mode in ("graph", "persistent", "per_view"):
-        for k in range(args.warmup):
-            step(k, mode)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush(k)
-            batch.set_views([dict(v, jitter_frame=args.warmup + k) for v in views])
-            evs[k][0].record(stream)
-            if mode == "graph":
-                batch.render(graph=True)
-            elif mode == "persistent":
-                batch.render()
-            else:
-                batch.render_per_view()
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        res[mode] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    r = batched_measure(vol, views, prm, args.steps, args.warmup, local)
     clk.__exit__()
-    ms = res["graph"]
-    value = samples / (ms * 1e-3) / 1e9
+    ms = r["ms_graph"]
     line = {"metric": "Gsamples/s, 64 uneven views in one persistent launch (CUDA graph)",
-            "value": value * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "value": r["gsamples_s"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched-64", "views": 64, "pixels": pixels,
                        "sizes": "256x256..1920x1080 seeded", "steps": "{8,16,32,128}",
                        "light_steps": 6, "volume_precision": prec,
                        "l2": "flushed between steps (256 MiB write + 256 MiB read, untimed)",
-                       "launch_config": best, "tile_shape_and_steps_per_iteration":
-                       list(_native.config_parts(best)), "config_ms": times},
-            "ms_persistent_no_graph": res["persistent"], "ms_one_launch_per_view": res["per_view"],
-            "speedup_vs_per_view": res["per_view"] / ms,
+                       "launch_config": r["launch_config"],
+                       "tile_shape_and_steps_per_iteration": r["tile_shape_and_steps_per_iteration"],
+                       "config_ms": r["config_ms"]},
+            "ms_persistent_no_graph": r["ms_persistent_no_graph"],
+            "ms_one_launch_per_view": r["ms_one_launch_per_view"],
+            "speedup_vs_per_view": r["speedup_vs_per_view"],
             "gpu_launches": args.steps, "clocks": dict(clk.summary(), window="all modes")}
     if rank == 0:
         print(json.dumps(line))
-    batch.close()
     return 0
 
 
-def run_served(args):
-    """Serving workload: Poisson arrivals at 2000 requests/s over 256 sessions;
-    each request is the next TAA frame of its session (camera on the session's
-    orbit, 640x360..1920x1080, 8 or 16 steps, FP16 history on the device).
-    Measured twice on the same arrival trace: continuous batching (up to 64
-    requests per persistent launch, two batches in flight) and the plain
-    per-frame form (one request per launch set, one at a time).  Latency is
-    submit -> device work complete; frames/s is also taken with every request
-    queued at once (saturation)."""
+def served_measure(vol, prm, n_req, n_warm, rank=0, oracle_frames=0):
+    """Config 5: Poisson arrivals at 2000 requests/s over 256 sessions
+    (640x360..1920x1080, 8 or 16 steps, FP16 history), the same trace served by
+    continuous batching (<= 64 requests per persistent launch, two batches in
+    flight) and by the plain per-frame form (one request per launch set, one in
+    flight), paced and saturated (all requests queued at once).  Latency is
+    submit -> device work complete.  Optionally the max-abs error of a served
+    640x360 session over `oracle_frames` frames against the FP64 oracle chain
+    (render -> motion -> TAA)."""
     import numpy as np
-    import torch
 
-    from paper_1609_05344_gb300 import _native, api, inputs as I
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    _native.build()
-    prec = args.precision if args.precision_set else "fp16"
-    vol = api.Volume(I.volume_desc("full", seed=3, precision=prec))
-    prm = I.params()
+    from paper_1609_05344_gb300 import api, inputs as I
     rng = np.random.default_rng(55 + rank)
     n_sess = 256
     sizes = [(int(rng.integers(640, 1921)), int(rng.integers(360, 1081))) for _ in range(n_sess)]
-    n_req = max(1, args.steps) * 125
-    n_warm = max(3, args.warmup) * 25
 
     def trace(seed, n):
         r = np.random.default_rng(seed)
@@ -604,8 +648,6 @@ def run_served(args):
             max_batch_views=1, slots=1)
         srv = api.Server(vol, prm, history_fmt="fp16", max_sessions=n_sess, **cfg)
         sids = [srv.open_session(w, h) for (w, h) in sizes]
-        frame = [0] * n_sess
-        # warm-up requests (untimed)
         wt = [srv.submit(sids[k % n_sess], I.orbit_camera(0, 100 + k % n_sess), 8)
               for k in range(n_warm)]
         for t in wt:
@@ -632,26 +674,76 @@ def run_served(args):
 
     t_arr, sess, steps = trace(7 + rank, n_req)
     res = {}
-    clk = ClockSampler(local).__enter__()
     for mode in ("continuous", "per_frame"):
         res[mode] = run(mode, t_arr, sess, steps, paced=True)
         res[mode + "_saturated"] = run(mode, t_arr, sess, steps, paced=False)
+    out = {"requests": n_req, "sessions": n_sess, "arrivals": "Poisson 2000/s",
+           "mean_pixels_per_request": float(np.mean([sizes[int(k)][0] * sizes[int(k)][1]
+                                                     for k in sess])),
+           "p50_ms": res["continuous"]["p50_ms"], "p99_ms": res["continuous"]["p99_ms"],
+           "frames_per_s_saturated": res["continuous_saturated"]["frames_per_s"],
+           "per_frame_p50_ms": res["per_frame"]["p50_ms"],
+           "per_frame_p99_ms": res["per_frame"]["p99_ms"],
+           "per_frame_frames_per_s_saturated": res["per_frame_saturated"]["frames_per_s"],
+           "speedup_saturated": (res["continuous_saturated"]["frames_per_s"]
+                                 / res["per_frame_saturated"]["frames_per_s"]),
+           "runs": res}
+    if oracle_frames:
+        from oracle import oracle as O
+        w, h = 640, 360
+        srv = api.Server(vol, prm, history_fmt="fp16", max_batch_views=8, slots=2)
+        sid, other = srv.open_session(w, h), srv.open_session(1920, 1080)
+        ovol = O.Volume(dict(vol.desc, precision="fp32"))
+        ohist, worst = None, 0.0
+        for f in range(oracle_frames):
+            cam = I.orbit_camera(f, 100)
+            t1 = srv.submit(sid, cam, 8)
+            t2 = srv.submit(other, I.orbit_camera(f, 101), 16)  # batched beside a large view
+            srv.wait(t1)
+            srv.wait(t2)
+            ocur, _ = O.render(ovol, cam, prm, w, h, 8, 6, jitter_frame=f,
+                               nthreads=os.cpu_count() or 1)
+            omot = (O.motion(vol.desc, prm, I.orbit_camera(f - 1, 100), cam, w, h) if f
+                    else np.zeros((h, w, 2)))
+            ohist = O.taa(ohist, ocur, omot, blend=0.1)
+            worst = max(worst, float(np.abs(srv.output(sid).astype(np.float64) - ohist).max()))
+        srv.close()
+        ovol.close()
+        out["max_abs_err_vs_fp64"] = worst
+        out["err_sample"] = (f"every pixel of a served 640x360 session (batched with a 1920x1080 "
+                             f"one) over {oracle_frames} frames, against the oracle chain")
+    return out
+
+
+def run_served(args):
+    """Serving workload (config 5): see served_measure."""
+    import torch
+
+    from paper_1609_05344_gb300 import _native, api, inputs as I
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _native.build()
+    prec = args.precision if args.precision_set else "fp16"
+    vol = api.Volume(I.volume_desc("full", seed=3, precision=prec))
+    prm = I.params()
+    clk = ClockSampler(local).__enter__()
+    r = served_measure(vol, prm, max(1, args.steps) * 125, max(3, args.warmup) * 25, rank)
     clk.__exit__()
-    pix = float(np.mean([sizes[int(k)][0] * sizes[int(k)][1] for k in sess]))
     line = {"metric": "served frames/s (saturated) and p50/p99 latency at 2000 req/s, 256 sessions",
-            "value": res["continuous_saturated"]["frames_per_s"] * world, "unit": "frames/s",
+            "value": r["frames_per_s_saturated"] * world, "unit": "frames/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / res["continuous_saturated"]["frames_per_s"],
+            "ms_per_step": 1e3 / r["frames_per_s_saturated"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "served", "sessions": n_sess, "requests": n_req,
+            "config": {"workload": "served", "sessions": r["sessions"], "requests": r["requests"],
                        "arrivals": "Poisson 2000/s", "sizes": "640x360..1920x1080 seeded",
                        "steps": "{8,16}", "light_steps": 6, "history": "fp16",
-                       "volume_precision": prec, "mean_pixels_per_request": pix,
+                       "volume_precision": prec,
+                       "mean_pixels_per_request": r["mean_pixels_per_request"],
                        "continuous": "<=64 requests per persistent launch, 2 in flight",
                        "per_frame": "1 request per launch set, 1 in flight"},
-            "p50_ms": res["continuous"]["p50_ms"], "p99_ms": res["continuous"]["p99_ms"],
-            "served": res, "clocks": dict(clk.summary(), window="all runs")}
+            "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+            "served": r["runs"], "clocks": dict(clk.summary(), window="all runs")}
     if rank == 0:
         print(json.dumps(line))
     return 0
@@ -857,6 +949,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "unorm16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="fast-1080p only: skip the 64-view batch and serving summaries")
     ap.add_argument("--jitter", default="pixel", choices=["pixel", "frame", "none"],
                     help="fast-1080p start offsets: per pixel (Sec. 3.2), one per frame "
                          "(Sec. 4), or none (midpoint samples)")

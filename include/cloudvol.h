@@ -424,6 +424,23 @@ int cloud_session_wait_frame(cloud_session *s, int frame_index, int timeout_ms);
  * clears a CLOUD_ERR_TIMEOUT state. */
 int cloud_session_reset(cloud_session *s);
 
+/* Checkpoint of a session: the state its next frame depends on -- the latest
+ * resolved frame (the history Sec. 3.2 reprojects), whether there is one, the
+ * frame index (the next jitter frame) and the previous camera -- copied to or
+ * from caller-owned host memory of cloud_session_snapshot_bytes bytes (a
+ * header, then width*height*4 history values).  cloud_session_snapshot
+ * enqueues the copy on `stream` (after the session's frames issued on that
+ * stream) and waits for it; it refuses a session in the CLOUD_ERR_TIMEOUT
+ * state.  cloud_session_restore loads a snapshot into a session of the same
+ * size and history format (a fresh one, or one on another device), waiting
+ * for the copy and for the session's own read-backs; its next frame then
+ * continues exactly as the snapshotted session's would (bitwise the same
+ * pixels).  A buffer that is not a snapshot of this size and format is
+ * CLOUD_ERR_INVALID_ARG.  Checkpointing has no counterpart in the paper. */
+int cloud_session_snapshot_bytes(const cloud_session *s, size_t *bytes);
+int cloud_session_snapshot(cloud_session *s, void *dst, size_t bytes, void *stream);
+int cloud_session_restore(cloud_session *s, const void *src, size_t bytes, void *stream);
+
 /* ---- continuous-batching render server ----------------------------------- */
 
 /* A server renders TAA frames (as cloud_session_frame, Sec. 3.2) for many

@@ -158,6 +158,9 @@ SIGNATURES = [
     ("cloud_session_frame_async", _i, [_vp, _P(Camera), _P(Params), _i, _i, _i, ctypes.c_float,
                                        _vp, _ip, _vp]),
     ("cloud_session_wait_frame", _i, [_vp, _i, _i]),
+    ("cloud_session_snapshot_bytes", _i, [_vp, _P(ctypes.c_size_t)]),
+    ("cloud_session_snapshot", _i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    ("cloud_session_restore", _i, [_vp, _vp, ctypes.c_size_t, _vp]),
     ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
     ("cloud_debug_set_wait_polls", _i, [_i]),
     ("cloud_debug_set_occupancy", _i, [_i]),

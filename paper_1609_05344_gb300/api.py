@@ -246,6 +246,22 @@ class Session:
     def reset(self):
         N.check(N.lib().cloud_session_reset(self._h), "cloud_session_reset")
 
+    def snapshot(self, stream=None) -> bytes:
+        """Checkpoint of the session's state (cloud_session_snapshot) as bytes."""
+        n = ctypes.c_size_t()
+        N.check(N.lib().cloud_session_snapshot_bytes(self._h, ctypes.byref(n)),
+                "cloud_session_snapshot_bytes")
+        buf = ctypes.create_string_buffer(n.value)
+        N.check(N.lib().cloud_session_snapshot(self._h, buf, n.value, _stream(stream)),
+                "cloud_session_snapshot")
+        return buf.raw
+
+    def restore(self, snap: bytes, stream=None):
+        """Load a checkpoint taken by snapshot() (cloud_session_restore)."""
+        buf = ctypes.create_string_buffer(bytes(snap), len(snap))
+        N.check(N.lib().cloud_session_restore(self._h, buf, len(snap), _stream(stream)),
+                "cloud_session_restore")
+
     def _frame_bytes(self) -> int:
         return self.width * self.height * (16 if self.history_fmt == "fp32" else 8)
 

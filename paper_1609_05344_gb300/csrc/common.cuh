@@ -102,6 +102,10 @@ __device__ __forceinline__ df df_add(df a, df b) {
     const df s = two_sum(a.hi, b.hi);
     return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
+__device__ __forceinline__ df df_addf(df a, float b) {
+    const df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_mul(df a, df b) {
     const float p = a.hi * b.hi;
@@ -175,16 +179,25 @@ inline void split_df10(double v, float *hi, float *lo) {
 //            from the dx = 0 half (rounded at packing exactly as the x lerp
 //            would round them);
 //   UNORM16  each texel as 16-bit fixed point q = round((t + 1/2) 2^16);
-//   FP16 / BF16  corner 0 as 16-bit fixed point (as UNORM16) and the other
+//   FP16 / BF16  corner 0 as 16-bit fixed point (as UNORM16), the other dx = 0
 //            corners as IEEE half (bfloat16) differences from that decoded
-//            corner 0.  Neighbouring texels differ little, so the 11-bit (8-bit)
-//            significand rounds a small difference instead of the texel itself.
-// A loader returns the corners relative to an offset, with the dx = 1 half
-// as differences from the dx = 0 half (the operand the x lerp needs), and
-// returns the offset: the centred texel value at a point is the lerp of the
-// returned corners plus the offset (0 for FP32 records; -3/2 for UNORM16,
-// whose corners decode to 1 + q 2^-16 by bit operations; the decoded corner 0
-// for the difference records, whose corner 0 is then 0).
+//            corner 0, and the dx = 1 corners as differences from the decoded
+//            dx = 0 corner next to them.  Neighbouring texels differ little, so
+//            the 11-bit (8-bit) significand rounds a small difference instead
+//            of the texel itself.
+// A loader returns the corners with the dx = 1 half as differences from the
+// dx = 0 half (the operand the x lerp needs) and returns an offset: the lerp
+// of the returned corners plus the offset, minus texel_bias<T>(), is the
+// centred texel value at a point.  FP32 records: offset 0, bias 0.  UNORM16:
+// corners decoded to 1 + q 2^-16 by bit operations, offset 0, bias 3/2.
+// FP16 / BF16: corners relative to corner 0 (so corner 0 is 0), offset the
+// decoded corner 0 as 1 + q 2^-16, bias 3/2.  The bias is folded into the
+// density's constants (SceneParams::k0, w_off).
+template <typename T>
+__host__ __device__ constexpr float texel_bias() { return 1.5f; }
+template <>
+__host__ __device__ constexpr float texel_bias<float>() { return 0.0f; }
+inline float texel_bias_of(int precision) { return precision == CLOUD_PRECISION_FP32 ? 0.0f : 1.5f; }
 
 // An FP32 record is one 32-byte sector, fetched by a single 256-bit load
 // (sm_100+ ld.global .v8): one L1 wavefront instead of two.
@@ -233,42 +246,35 @@ __device__ __forceinline__ float load_rec8(const uint16_t *tile, uint32_t rec, f
     const float2 d0 = __fadd2_rn(make_float2(unorm_lo(r.z), unorm_hi(r.z)), make_float2(-c[0], -c[1]));
     const float2 d1 = __fadd2_rn(make_float2(unorm_lo(r.w), unorm_hi(r.w)), make_float2(-c[2], -c[3]));
     c[4] = d0.x; c[5] = d0.y; c[6] = d1.x; c[7] = d1.y;
-    return -1.5f;
+    return 0.0f;
 }
 __device__ __forceinline__ float load_rec4(const uint16_t *tile, uint32_t rec, float c[4]) {
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(tile) + rec);
     c[0] = unorm_lo(r.x); c[1] = unorm_hi(r.x);
     const float2 d = __fadd2_rn(make_float2(unorm_lo(r.y), unorm_hi(r.y)), make_float2(-c[0], -c[1]));
     c[2] = d.x; c[3] = d.y;
-    return -1.5f;
+    return 0.0f;
 }
 
-// Difference records (FP16 / BF16 volumes): relative corners (0, d1, .., d7).
+// Difference records (FP16 / BF16 volumes): relative corners (0, d1, d2, d3)
+// of the dx = 0 face and the x differences of the dx = 1 face, as stored.
 template <typename T>
 __device__ __forceinline__ float load_rec8(const T *tile, uint32_t rec, float c[8]) {
     const uint4 r = __ldg(reinterpret_cast<const uint4 *>(tile) + rec);
-    const float c0 = unorm_lo(r.x) - 1.5f;
     c[0] = 0.0f;
     c[1] = f16_hi(r.x, tile);
     unpack16(r.y, tile, c[2], c[3]);
-    float d5, d6, d7;
-    unpack16(r.z, tile, c[4], d5);
-    unpack16(r.w, tile, d6, d7);
-    c[5] = d5 - c[1];  // dx = 1 minus dx = 0 (corner 4 minus corner 0 = d4)
-    const float2 d = __fadd2_rn(make_float2(d6, d7), make_float2(-c[2], -c[3]));
-    c[6] = d.x; c[7] = d.y;
-    return c0;
+    unpack16(r.z, tile, c[4], c[5]);
+    unpack16(r.w, tile, c[6], c[7]);
+    return unorm_lo(r.x);
 }
 template <typename T>
 __device__ __forceinline__ float load_rec4(const T *tile, uint32_t rec, float c[4]) {
     const uint2 r = __ldg(reinterpret_cast<const uint2 *>(tile) + rec);
-    const float c0 = unorm_lo(r.x) - 1.5f;
     c[0] = 0.0f;
     c[1] = f16_hi(r.x, tile);
-    float d3;
-    unpack16(r.y, tile, c[2], d3);
-    c[3] = d3 - c[1];
-    return c0;
+    unpack16(r.y, tile, c[2], c[3]);
+    return unorm_lo(r.x);
 }
 
 // Host side of the multi-view resolve (taa.cu), used by the render server:

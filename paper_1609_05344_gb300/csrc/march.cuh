@@ -30,7 +30,7 @@
 namespace cloudvol {
 
 #ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX
-#define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX 5
+#define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX 6
 #endif
 template <typename T, bool FX>
 struct MarchBlocks { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_16; };
@@ -43,6 +43,19 @@ struct MarchBlocks<float, true> { static constexpr int value = CLOUDVOL_MARCH_MI
 // compile-time constants: with FX the record-index and weight shifts of every
 // lookup are immediates instead of per-launch values.
 constexpr int kStdLog2Base = 7, kStdLog2Detail = 5, kStdLog2Weather = 9;
+
+// Light samples of a march evaluated per iteration of the light loop (the
+// density code is inlined that many times).
+#ifndef CLOUDVOL_LIGHT_UNROLL_F32
+#define CLOUDVOL_LIGHT_UNROLL_F32 6
+#endif
+#ifndef CLOUDVOL_LIGHT_UNROLL_16
+#define CLOUDVOL_LIGHT_UNROLL_16 2
+#endif
+template <typename T>
+struct LightUnroll { static constexpr int value = CLOUDVOL_LIGHT_UNROLL_16; };
+template <>
+struct LightUnroll<float> { static constexpr int value = CLOUDVOL_LIGHT_UNROLL_F32; };
 
 enum Axis { kBX = 0, kBY, kBZ, kDX, kDY, kDZ, kWX, kWY, kLatticeAxes };
 
@@ -58,7 +71,9 @@ struct SceneParams {
     float h_lo_scale, h_hi_scale;  // 10/thickness, 2.5/thickness, per 2^-16 m
     float sun[3], sun_rad[3], ambient[3];
     float hg_g, hg_norm, absorption, light_step, tau_max;  // hg_norm = (1 - g^2)/(4 pi)
-    float k0, inv_1mc, detail_w, rho0;
+    // k0 = 1/2 - c - w_d/2 minus the record decode bias b folded in:
+    // k0 - b + w_d b; w_off = 1/2 - b (weather values are stored centred)
+    float k0, inv_1mc, detail_w, rho0, w_off;
     // occupancy grid of the volume (bit set: density may be > 0 somewhere in
     // the 2x2x2-record macro-cell), or nullptr; log2 of its cells per axis
     const uint32_t *occ;
@@ -172,14 +187,32 @@ __device__ __forceinline__ float bilerp(const float c[4], int L, uint32_t cx, ui
     return fmaf(fy, xy.y - xy.x, xy.x);
 }
 
+// Height profile g(h) of the layer at a fixed-point height (2^-16 m above the
+// layer bottom): clamp(h / 0.1, 0, 1) clamp((1 - h) / 0.4, 0, 1), h in layer
+// thicknesses.
+__device__ __forceinline__ float height_profile(const SceneParams &p, int32_t hq) {
+    const float ga = fminf(fmaxf((float)hq * p.h_lo_scale, 0.0f), 1.0f);
+    const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
+    return ga * gb;
+}
+
+// Occupancy bit of the macro-cell holding a sample's base record: clear where
+// the volume's bound proves B - w_d Dt - c < 0, i.e. zero density.
+template <bool FX>
+__device__ __forceinline__ bool occupied(const SceneParams &p, uint32_t bx, uint32_t by, uint32_t bz) {
+    // macro-cell = record index >> 1 on each axis; bits x fastest
+    const int lo = FX ? kStdLog2Base - 1 : p.log2_occ, sh = 32 - lo;
+    const uint32_t cell = ((bz >> sh) << (2 * lo)) | ((by >> sh) << lo) | (bx >> sh);
+    return (__ldg(p.occ + (cell >> 5)) >> (cell & 31u)) & 1u;
+}
+
 // Density at a sample (Sec. 1):
 //   rho = g(h) W max(0, (B - w_d Dt - c)/(1 - c)),
-// tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0.
-// Samples outside the layer (g = 0) return without touching memory, and so do
-// samples in a macro-cell of the occupancy grid whose bound proves
-// B - w_d Dt - c < 0 everywhere in it: the value returned, 0, is exactly the
-// one the full evaluation gives there.  Otherwise the three record loads are
-// issued together so that one memory round trip serves the lookup.
+// tiles stored centred (value - 1/2), so (B - w_d Dt - c) = Bc - w_d Dtc + k0;
+// the records' decode bias is folded into k0 and w_off.
+// Samples outside the layer (g = 0) return without touching memory; the
+// three record loads are issued together so that one memory round trip serves
+// the lookup.
 template <bool FX, typename T>
 __device__ __forceinline__ float density(const SceneParams &p, const T *__restrict__ base,
                                          const T *__restrict__ detail,
@@ -188,16 +221,8 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
     const int lb = FX ? kStdLog2Base : p.log2_base, ld = FX ? kStdLog2Detail : p.log2_detail,
               lw = FX ? kStdLog2Weather : p.log2_weather;
     if (!FX && p.constant_mode) return p.rho0;
-    const float ga = fminf(fmaxf((float)hq * p.h_lo_scale, 0.0f), 1.0f);
-    const float gb = fminf(fmaxf((float)(p.h_top - hq) * p.h_hi_scale, 0.0f), 1.0f);
-    const float g = ga * gb;
+    const float g = height_profile(p, hq);
     if (g <= 0.0f) return 0.0f;
-    if (p.occ) {
-        // macro-cell = record index >> 1 on each axis; bits x fastest
-        const int lo = FX ? kStdLog2Base - 1 : p.log2_occ, sh = 32 - lo;
-        const uint32_t cell = ((c[kBZ] >> sh) << (2 * lo)) | ((c[kBY] >> sh) << lo) | (c[kBX] >> sh);
-        if (!((__ldg(p.occ + (cell >> 5)) >> (cell & 31u)) & 1u)) return 0.0f;
-    }
     float cb[8], cd[8], cw[4];
     const float ob = load_rec8(base, rec3(lb, c[kBX], c[kBY], c[kBZ]), cb);
     float od = 0.0f, ow = 0.0f;
@@ -210,13 +235,19 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
         r = fmaf(-p.detail_w, dt, r);
     }
     r = fmaxf(r * p.inv_1mc, 0.0f);
-    const float w = (FX || weather) ? bilerp(cw, lw, c[kWX], c[kWY]) + ow + kCentre : 1.0f;
+    const float w = (FX || weather) ? bilerp(cw, lw, c[kWX], c[kWY]) + ow + p.w_off : 1.0f;
     return g * w * r;
 }
 
-__device__ __forceinline__ df df_addf(df a, float b) {
-    const df s = two_sum(a.hi, b);
-    return fast_two_sum(s.hi, s.lo + a.lo);
+// Coordinates of view step i of ray `ow` of the warp from its staged start and
+// increment (integer arithmetic: the same values as adding the increment step
+// by step).
+__device__ __forceinline__ int32_t step_coords(const uint32_t (&c0)[kAxes][32],
+                                               const uint32_t (&e)[kAxes][32], unsigned ow,
+                                               uint32_t i, uint32_t cs[kLatticeAxes]) {
+#pragma unroll
+    for (int a = 0; a < kLatticeAxes; ++a) cs[a] = c0[a][ow] + i * e[a][ow];
+    return (int32_t)(c0[kLatticeAxes][ow] + i * e[kLatticeAxes][ow]);
 }
 
 // sigma D of one step, rounded the same way wherever it is recomputed
@@ -226,14 +257,19 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 
 // The march of one CTA pixel tile (4 warps, one pixel per lane).  View steps
 // are processed in chunks of CH:
-//   A  each lane evaluates its view densities and its early out (the optical
-//      depth does not depend on the lighting);
+//   A  view densities and the early out (the optical depth does not depend on
+//      the lighting): each lane marks which of its steps need a lookup (inside
+//      the layer, occupied macro-cell), the warp shares those lookups out over
+//      all 32 lanes, two per lane at a time, and each lane then walks its own
+//      steps in order for the optical depth and the early out;
 //   B  the warp shares out every (step, lane) light march with density > 0
 //      over all 32 lanes, so lanes whose own rays are empty, finished or
 //      outside the layer do useful work;
 //   C  each lane integrates its steps in order with the light sums from B.
-// The arithmetic of every sample is the same as a per-lane march.  Returns the
-// number of density lookups this lane performed.
+// The arithmetic of every sample is the same as a per-lane march (a skipped
+// lookup is one whose density is exactly 0).  Returns the number of density
+// lookups this lane's ray performed in the method's sense (Sec. 1: one per
+// view step walked, plus the light steps of each step with density).
 template <typename T, int LS, int SHAPE, bool FX, int CH>
 __device__ __forceinline__ unsigned long long march_tile(
     const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch<CH> &ws,
@@ -336,7 +372,48 @@ __device__ __forceinline__ unsigned long long march_tile(
     const unsigned lt_mask = (1u << lane) - 1u;
     float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     for (int i0 = 0; i0 < v.steps && __any_sync(kFull, alive); i0 += CH) {
-        // --- A: view densities and early out --------------------------------
+        // --- A1: which of this lane's CH steps need a density lookup: inside the
+        //     layer and in an occupied macro-cell of the occupancy grid (the grid
+        //     words of all CH steps are loaded together) -------------------------
+        uint32_t need = 0;
+        if (alive) {
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                if (i0 + k >= v.steps) break;
+                bool nd = true;
+                if (FX || !p.constant_mode) {
+                    nd = height_profile(p, hq + k * eh) > 0.0f;
+                    if (nd && p.occ)
+                        nd = occupied<FX>(p, c[kBX] + k * e[kBX], c[kBY] + k * e[kBY],
+                                          c[kBZ] + k * e[kBZ]);
+                }
+                if (nd) need |= 1u << k;
+            }
+        }
+        // --- A2: those (step, lane) lookups shared out over the warp, two per
+        //     lane at a time so that their record loads overlap (a3) -----------
+        unsigned nq = 0;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const unsigned m = __ballot_sync(kFull, (need >> k) & 1u);
+            if ((need >> k) & 1u) ws.pairs[nq + __popc(m & lt_mask)] = (uint16_t)((k << 5) | lane);
+            nq += __popc(m);
+        }
+        __syncwarp();
+        for (unsigned q = lane; q < nq; q += 64) {
+            // a lane without a second lookup repeats its first (same value, same entry)
+            const unsigned pa = ws.pairs[q], pb = ws.pairs[q + 32 < nq ? q + 32 : q];
+            uint32_t ca[kLatticeAxes], cq[kLatticeAxes];
+            const int32_t ha = step_coords(ws.c0, ws.e, pa & 31u, (uint32_t)i0 + (pa >> 5), ca);
+            const int32_t hb = step_coords(ws.c0, ws.e, pb & 31u, (uint32_t)i0 + (pb >> 5), cq);
+            const float ra = density<FX>(p, base, detail, weather, ca, ha);
+            const float rb = density<FX>(p, base, detail, weather, cq, hb);
+            ws.rho[pa >> 5][pa & 31u] = ra;
+            ws.rho[pb >> 5][pb & 31u] = rb;
+        }
+        __syncwarp();
+        // --- A3: each lane walks its steps in order: optical depth and the early
+        //     out (a7, Sec. 1: stop once alpha is ~1) ---------------------------
         uint32_t act = 0;
         int nA = 0;
         if (alive) {
@@ -344,18 +421,12 @@ __device__ __forceinline__ unsigned long long march_tile(
 #pragma unroll 1
             for (int k = 0; k < CH; ++k) {
                 if (i0 + k >= v.steps) break;
-                // --- a3: density lookup ---------------------------------------
-                const float rho = density<FX>(p, base, detail, weather, c, hq);
-                ws.rho[k][lane] = rho;
+                const float rho = ((need >> k) & 1u) ? ws.rho[k][lane] : 0.0f;
                 nA = k + 1;
                 if (rho > 0.0f) {
                     act |= 1u << k;
                     tau_a = __fadd_rn(tau_a, step_depth(p.absorption, rho, Df));
                 }
-#pragma unroll
-                for (int a = 0; a < kLatticeAxes; ++a) c[a] += e[a];
-                hq += eh;
-                // --- a7: early out once alpha is ~1 (Sec. 1) --------------------
                 if (tau_a >= p.tau_max) {
                     alive = false;
                     break;
@@ -363,6 +434,9 @@ __device__ __forceinline__ unsigned long long march_tile(
             }
             n_look += nA + nlight * __popc(act);
         }
+#pragma unroll
+        for (int a = kBX; a <= kBZ; ++a) c[a] += CH * e[a];
+        hq += CH * eh;
         if (!__any_sync(kFull, act != 0u)) continue;  // no density in this chunk, warp-wide
         // --- B: light marches shared out over the warp (a4, Sec. 1) ----------
         unsigned offs[CH + 1];
@@ -376,19 +450,26 @@ __device__ __forceinline__ unsigned long long march_tile(
         __syncwarp();
         for (unsigned q = lane; q < offs[CH]; q += 32) {
             const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
-            const uint32_t i = (uint32_t)(i0 + (int)k);
             uint32_t cs[kLatticeAxes];
-#pragma unroll
-            for (int a = 0; a < kLatticeAxes; ++a) cs[a] = ws.c0[a][ow] + i * ws.e[a][ow];
-            const int32_t hs = (int32_t)(ws.c0[kLatticeAxes][ow] + i * ws.e[kLatticeAxes][ow]);
+            const int32_t hs = step_coords(ws.c0, ws.e, ow, (uint32_t)(i0 + (int)k), cs);
             float rho_sum = 0.0f;
+            if (LS >= 0) {
+                constexpr int kU = LightUnroll<T>::value;
+#pragma unroll kU
+                for (int j = 0; j < (LS >= 0 ? LS : 0); ++j) {
+                    uint32_t cj[kLatticeAxes];
 #pragma unroll
-            for (int j = 0; j < (LS >= 0 ? LS : CLOUD_MAX_LIGHT_STEPS); ++j) {
-                if (LS < 0 && j >= nlight) break;
-                uint32_t cj[kLatticeAxes];
+                    for (int a = 0; a < kLatticeAxes; ++a) cj[a] = cs[a] + p.loff[j][a];
+                    rho_sum += density<FX>(p, base, detail, weather, cj, hs + p.lh[j]);
+                }
+            } else {
+#pragma unroll 2
+                for (int j = 0; j < nlight; ++j) {
+                    uint32_t cj[kLatticeAxes];
 #pragma unroll
-                for (int a = 0; a < kLatticeAxes; ++a) cj[a] = cs[a] + p.loff[j][a];
-                rho_sum += density<FX>(p, base, detail, weather, cj, hs + p.lh[j]);
+                    for (int a = 0; a < kLatticeAxes; ++a) cj[a] = cs[a] + p.loff[j][a];
+                    rho_sum += density<FX>(p, base, detail, weather, cj, hs + p.lh[j]);
+                }
             }
             ws.lsum[k][ow] = rho_sum;
         }

@@ -78,7 +78,9 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
     p->tau_max = prm->tau_max > 0.0 ? (float)prm->tau_max : INFINITY;
     const double wd = vol->log2_detail ? d.detail_weight : 0.0;
     p->detail_w = (float)wd;
-    p->k0 = (float)(0.5 - d.coverage - 0.5 * wd);
+    const double bias = texel_bias_of(d.precision);
+    p->k0 = (float)(0.5 - d.coverage - 0.5 * wd - bias + wd * bias);
+    p->w_off = (float)(0.5 - bias);
     p->inv_1mc = (float)(1.0 / (1.0 - d.coverage));
     p->rho0 = (float)d.constant_density;
     p->occ = noise && g_use_occupancy.load() ? vol->occ : nullptr;

@@ -243,3 +243,88 @@ extern "C" int cloud_session_wait_frame(cloud_session *s, int frame_index, int t
         std::this_thread::yield();
     }
 }
+
+// ---------------------------------------------------------------------------
+// Snapshot / restore: the state a session needs to continue -- its latest
+// resolved frame (the history the next resolve reprojects), whether it has
+// one, its frame index (the next jitter frame) and the previous camera -- as
+// one block of host memory: a header followed by the history pixels.
+namespace {
+constexpr uint32_t kSnapMagic = 0x43564C53u;  // "SLVC"
+constexpr uint32_t kSnapVersion = 1;
+struct SnapHeader {
+    uint32_t magic, version;
+    int32_t width, height, fmt, has_history, frame, reserved;
+    cloud_camera prev_cam;
+};
+}  // namespace
+
+extern "C" int cloud_session_snapshot_bytes(const cloud_session *s, size_t *bytes) {
+    clear_error();
+    if (!s || !bytes) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_snapshot_bytes: null pointer");
+    *bytes = sizeof(SnapHeader) + frame_bytes(s);
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_session_snapshot(cloud_session *s, void *dst, size_t bytes, void *stream) {
+    clear_error();
+    if (!s || !dst) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_snapshot: null pointer");
+    if (bytes != sizeof(SnapHeader) + frame_bytes(s))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_snapshot: wrong size (see cloud_session_snapshot_bytes)");
+    if (int rc = check_waits(s, "cloud_session_snapshot")) return rc;
+    SnapHeader h{};
+    h.magic = kSnapMagic;
+    h.version = kSnapVersion;
+    h.width = s->width;
+    h.height = s->height;
+    h.fmt = s->fmt;
+    h.has_history = s->has_history ? 1 : 0;
+    h.frame = s->frame;
+    h.prev_cam = s->prev_cam;
+    std::memcpy(dst, &h, sizeof(h));
+    char *pix = static_cast<char *>(dst) + sizeof(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->has_history) {
+        if (int rc = check_cuda(cudaMemcpyAsync(pix, s->hist[s->latest], frame_bytes(s),
+                                                cudaMemcpyDeviceToHost, st),
+                                "cloud_session_snapshot: copy history"))
+            return rc;
+        if (int rc = check_cuda(cudaStreamSynchronize(st), "cloud_session_snapshot")) return rc;
+    } else {
+        std::memset(pix, 0, frame_bytes(s));
+    }
+    return CLOUD_OK;
+}
+
+extern "C" int cloud_session_restore(cloud_session *s, const void *src, size_t bytes, void *stream) {
+    clear_error();
+    if (!s || !src) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_restore: null pointer");
+    if (bytes != sizeof(SnapHeader) + frame_bytes(s))
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_restore: wrong size for this session");
+    SnapHeader h;
+    std::memcpy(&h, src, sizeof(h));
+    if (h.magic != kSnapMagic || h.version != kSnapVersion)
+        return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_restore: not a session snapshot");
+    if (h.width != s->width || h.height != s->height || h.fmt != s->fmt)
+        return set_error(CLOUD_ERR_INVALID_ARG,
+                         "cloud_session_restore: snapshot of a session of another size or history format");
+    if (h.frame < 0) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_session_restore: bad frame index");
+    // read-backs still in flight from the history buffers finish first
+    if (int rc = check_cuda(cudaStreamSynchronize(s->copy_stream), "cloud_session_restore")) return rc;
+    s->copy_pending[0] = s->copy_pending[1] = false;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h.has_history) {
+        if (int rc = check_cuda(cudaMemcpyAsync(s->hist[0], static_cast<const char *>(src) + sizeof(h),
+                                                frame_bytes(s), cudaMemcpyHostToDevice, st),
+                                "cloud_session_restore: copy history"))
+            return rc;
+        if (int rc = check_cuda(cudaStreamSynchronize(st), "cloud_session_restore")) return rc;
+    }
+    s->latest = 0;
+    s->has_history = h.has_history != 0;
+    s->frame = h.frame;
+    s->prev_cam = h.prev_cam;
+    s->wait_seen = *reinterpret_cast<volatile unsigned int *>(s->h_wait);
+    s->wait_failed = false;
+    return CLOUD_OK;
+}

@@ -28,21 +28,35 @@ struct MotionParams {
     float kx, ky, kx1, ky1;  // aT'/aT, T'/T, and the same minus 1
     float sx, sy;            // W / (2 aT'), H / (2 T')
     int width, height, cam_in_layer;
-    // exact (FP64) restatement for near-tie layer-entry decisions
-    double v00[3], vx[3], vy[3], oz, slab_lo, slab_hi, t_max;
+    // double-float restatement of the world-space ray for near-tie layer-entry
+    // decisions: v(x, y) = v00 + x vx + y vy (vx, vy split so that x * hi is
+    // exact), slab_lo - o_z, slab_hi - o_z and the far clip
+    float v00h[3], v00l[3], vxh[3], vxl[3], vyh[3], vyl[3];
+    float zlo_h, zlo_l, zhi_h, zhi_l, tmax_h, tmax_l;
 };
 
 // Reprojection depth parameter lambda (t / |v|) of the layer entry point, or
-// of the far clip when the ray does not enter the layer ahead of the camera.
+// of the far clip when the ray does not enter the layer ahead of the camera,
+// in double-float FP32 (about 48 bits, the layer clip of the raymarch): for the
+// rays whose entry FP32 cannot decide.
 __device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, int y) {
-    double v[3];
-    for (int k = 0; k < 3; ++k) v[k] = fma((double)y, p.vy[k], fma((double)x, p.vx[k], p.v00[k]));
-    const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    const double dz = v[2] / n;
-    if (fabs(dz) < 1e-8) return (float)(p.t_max / n);
-    const double tl = (p.slab_lo - p.oz) / dz, th = (p.slab_hi - p.oz) / dz;
-    const double t0 = fmax(fmin(tl, th), 0.0), t1 = fmin(fmax(tl, th), p.t_max);
-    return (float)(((t1 > t0 && t0 > 0.0) ? t0 : p.t_max) / n);
+    const float xf = (float)x, yf = (float)y;
+    df r[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        df a = {p.v00h[k], p.v00l[k] + fmaf(xf, p.vxl[k], yf * p.vyl[k])};
+        a = df_addf(a, xf * p.vxh[k]);  // exact products
+        r[k] = df_addf(a, yf * p.vyh[k]);
+    }
+    const df n2 = df_add(df_add(df_mul(r[0], r[0]), df_mul(r[1], r[1])), df_mul(r[2], r[2]));
+    const df rn = df_rsqrt(n2);  // 1 / |v|
+    const df lam_max = df_mul({p.tmax_h, p.tmax_l}, rn);
+    if (fabsf(r[2].hi) * rn.hi < 1e-8f) return lam_max.hi;  // horizontal ray
+    const df inv = df_recip(r[2]);
+    const df ll = df_mul({p.zlo_h, p.zlo_l}, inv), lh = df_mul({p.zhi_h, p.zhi_l}, inv);
+    const df zero = {0.0f, 0.0f};
+    const df l0 = df_max(df_min(ll, lh), zero), l1 = df_min(df_max(ll, lh), lam_max);
+    return (df_gt(l1, l0) && df_gt(l0, zero)) ? l0.hi : lam_max.hi;
 }
 
 // Motion of one pixel.  The motion is a small difference of nearly equal
@@ -51,7 +65,8 @@ __device__ __noinline__ float entry_lambda_exact(const MotionParams &p, int x, i
 // three parts so that a thread can share the column terms between pixels and
 // interleave the arithmetic of several pixels: the column terms, the depth
 // parameter of the layer entry (FP32, with a flag for the near ties that the
-// FP64 restatement decides), and the projection into the previous camera.
+// double-float restatement decides), and the projection into the previous
+// camera.
 struct MotionCol {
     float a, n2x, vzx, gx0, gx1, gx2, akx, nx0;
 };
@@ -295,7 +310,7 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
     }
     // 2. motion (registers only) and the history footprint of both pixels
     //    (rows 2 ty and 2 ty + 1 of the tile): column terms once, the two
-    //    pixels' arithmetic interleaved, the rare FP64 near-tie calls after
+    //    pixels' arithmetic interleaved, the rare near-tie calls after
     bool use[2] = {false, false};
     float fxs[2] = {0.f, 0.f}, fys[2] = {0.f, 0.f};
     float4 h00[2], h01[2], h10[2], h11[2];
@@ -488,14 +503,13 @@ int build_motion_params(const cloud_volume *vol, const cloud_params *prm, const 
     const double a0 = (1.0 / width - 1.0) * aT, ax = 2.0 * aT / width;
     const double b0 = (1.0 - 1.0 / height) * T, by = -2.0 * T / height;
     for (int k = 0; k < 3; ++k) {
-        p->v00[k] = cur->forward[k] + a0 * cur->right[k] + b0 * cur->up[k];
-        p->vx[k] = ax * cur->right[k];
-        p->vy[k] = by * cur->up[k];
+        split_df(cur->forward[k] + a0 * cur->right[k] + b0 * cur->up[k], &p->v00h[k], &p->v00l[k]);
+        split_df10(ax * cur->right[k], &p->vxh[k], &p->vxl[k]);
+        split_df10(by * cur->up[k], &p->vyh[k], &p->vyl[k]);
     }
-    p->oz = cur->pos[2];
-    p->slab_lo = vol->desc.slab_lo_m;
-    p->slab_hi = vol->desc.slab_hi_m;
-    p->t_max = prm->t_max_m;
+    split_df(vol->desc.slab_lo_m - cur->pos[2], &p->zlo_h, &p->zlo_l);
+    split_df(vol->desc.slab_hi_m - cur->pos[2], &p->zhi_h, &p->zhi_l);
+    split_df(prm->t_max_m, &p->tmax_h, &p->tmax_l);
     return CLOUD_OK;
 }
 

@@ -139,16 +139,31 @@ __device__ __forceinline__ void store_record(uint16_t *dst, const double (&t)[R]
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[r] = encode_unorm16(t[r]);
 }
-// FP16 / BF16: corner 0 as 16-bit fixed point, the others as differences from
-// its decoded value, rounded once from FP64
+__device__ __forceinline__ double decode16(uint16_t u, const __half *) {
+    return (double)__half2float(__ushort_as_half(u));
+}
+__device__ __forceinline__ double decode16(uint16_t u, const __nv_bfloat16 *) {
+    return (double)__bfloat162float(__ushort_as_bfloat16(u));
+}
+// FP16 / BF16: corner 0 as 16-bit fixed point, the other dx = 0 corners as
+// differences from its decoded value, the dx = 1 corners as differences from
+// the decoded dx = 0 corner beside them; each rounded once from FP64, against
+// the values the loader will reconstruct
 template <typename T, int R>
 __device__ __forceinline__ void store_record(T *dst, const double (&t)[R]) {
     uint16_t *u = reinterpret_cast<uint16_t *>(dst);
     const uint16_t q0 = encode_unorm16(t[0]);
     const double c0 = decode_unorm16(q0);
+    double dec[R / 2];
     u[0] = q0;
+    dec[0] = c0;
 #pragma unroll
-    for (int r = 1; r < R; ++r) u[r] = encode16(t[r] - c0, dst);
+    for (int r = 1; r < R / 2; ++r) {
+        u[r] = encode16(t[r] - c0, dst);
+        dec[r] = c0 + decode16(u[r], dst);
+    }
+#pragma unroll
+    for (int r = R / 2; r < R; ++r) u[r] = encode16(t[r] - dec[r - R / 2], dst);
 }
 
 template <typename T>
@@ -203,7 +218,7 @@ __global__ void decode_kernel(const T *__restrict__ packed, int stride, float *_
 template <typename T>
 __device__ __forceinline__ void record_range(const T *tile, uint32_t rec, float &lo, float &hi) {
     float c[8];
-    const float off = load_rec8(tile, rec, c);
+    const float off = load_rec8(tile, rec, c) - texel_bias<T>();
     float v[8] = {c[0], c[1], c[2], c[3], c[0] + c[4], c[1] + c[5], c[2] + c[6], c[3] + c[7]};
     lo = hi = v[0] + off;
 #pragma unroll

@@ -283,6 +283,50 @@ def test_fused_resolve_random_camera_pairs(api, oracle):
     assert worst <= 1e-4
 
 
+@pytest.mark.parametrize("fmt", ["fp32", "fp16"])
+def test_session_snapshot_restore_continues_bitwise(api, fmt):
+    """A session checkpointed mid-orbit and restored into a fresh session
+    continues bitwise like the uninterrupted one (history, jitter index and
+    previous camera all carried over); malformed or mismatched snapshots are
+    refused."""
+    import torch
+    from paper_1609_05344_gb300 import _native as N
+    vol = api.Volume(I.volume_desc("full", seed=3))
+    prm = I.params()
+    w, h = 96, 54
+    dt = torch.float32 if fmt == "fp32" else torch.float16
+    a = api.Session(vol, w, h, history_fmt=fmt)
+    host = torch.empty((h, w, 4), dtype=dt, pin_memory=True)
+    for f in range(4):
+        a.frame(I.orbit_camera(f, 3), prm, 8, 6, host_out=host)
+    snap = a.snapshot()
+    cont = [a.frame(I.orbit_camera(f, 3), prm, 8, 6, host_out=torch.empty_like(host)).clone()
+            for f in range(4, 7)]
+    b = api.Session(vol, w, h, history_fmt=fmt)
+    b.frame(I.orbit_camera(30, 3), prm, 8, 6, host_out=host)  # state that the restore replaces
+    b.restore(snap)
+    got = [b.frame(I.orbit_camera(f, 3), prm, 8, 6, host_out=torch.empty_like(host)).clone()
+           for f in range(4, 7)]
+    for x, y in zip(cont, got):
+        assert torch.equal(x, y)
+    bad = bytearray(snap)
+    bad[0] ^= 0xFF
+    with pytest.raises(N.CloudError):
+        b.restore(bytes(bad))
+    other = api.Session(vol, w + 1, h, history_fmt=fmt)
+    with pytest.raises(N.CloudError):
+        other.restore(snap)
+    # a snapshot of a session without history restores to a first frame
+    fresh = api.Session(vol, w, h, history_fmt=fmt)
+    snap0 = fresh.snapshot()
+    b.restore(snap0)
+    x = b.frame(I.orbit_camera(0, 3), prm, 8, 6, host_out=torch.empty_like(host)).clone()
+    y = fresh.frame(I.orbit_camera(0, 3), prm, 8, 6, host_out=torch.empty_like(host)).clone()
+    assert torch.equal(x, y)
+    for sess in (a, b, other, fresh):
+        sess.close()
+
+
 def test_resolve_wait_give_up_is_reported(api):
     """The fused resolve's bounded wait for its tile copy, made to give up at
     once (poll budget 0): every tile's outputs stay unwritten, the give-ups are
