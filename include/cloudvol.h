@@ -248,7 +248,8 @@ int cloud_render_count(const cloud_volume *vol, const cloud_camera *cam, const c
  * config = shape + 4 * k, with shape the pixel tile of a 128-thread CTA (0:
  * 16x8, 1: 32x4 of 8x4-pixel warps, 2: 32x4 of 16x2-pixel warps, 3: 8x16) and
  * k selecting the view steps a warp evaluates per iteration of its march
- * (0: 8, 1: 16).  Every configuration gives bitwise the same pixels. */
+ * (0: 8, 1: 16).  Every configuration gives bitwise the same pixels.  Until a
+ * configuration is tuned or set, launches use 3 (8x16, 8 steps). */
 #define CLOUD_TUNE_CONFIGS 8
 
 /* Times every launch configuration of the raymarch on this workload (repeats

@@ -30,7 +30,7 @@
 namespace cloudvol {
 
 #ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX
-#define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX 6
+#define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX 7
 #endif
 template <typename T, bool FX>
 struct MarchBlocks { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_16; };
@@ -52,6 +52,18 @@ constexpr int kStdLog2Base = 7, kStdLog2Detail = 5, kStdLog2Weather = 9;
 #ifndef CLOUDVOL_LIGHT_UNROLL_16
 #define CLOUDVOL_LIGHT_UNROLL_16 2
 #endif
+// View lookups a lane evaluates per round of the shared-out view phase (their
+// record loads can overlap; more of them cost registers).
+#ifndef CLOUDVOL_VIEW_BATCH_F32
+#define CLOUDVOL_VIEW_BATCH_F32 1
+#endif
+#ifndef CLOUDVOL_VIEW_BATCH_16
+#define CLOUDVOL_VIEW_BATCH_16 2
+#endif
+template <typename T>
+struct ViewBatch { static constexpr int value = CLOUDVOL_VIEW_BATCH_16; };
+template <>
+struct ViewBatch<float> { static constexpr int value = CLOUDVOL_VIEW_BATCH_F32; };
 template <typename T>
 struct LightUnroll { static constexpr int value = CLOUDVOL_LIGHT_UNROLL_16; };
 template <>
@@ -382,7 +394,11 @@ __device__ __forceinline__ unsigned long long march_tile(
                 if (i0 + k >= v.steps) break;
                 bool nd = true;
                 if (FX || !p.constant_mode) {
-                    nd = height_profile(p, hq + k * eh) > 0.0f;
+                    // g(h) > 0 exactly when 0 < h < layer thickness: both clamp
+                    // factors are then at least ~1e-8, their product far above
+                    // the FP32 underflow, and otherwise one of them is 0
+                    const int32_t hk = hq + k * eh;
+                    nd = hk > 0 && hk < p.h_top;
                     if (nd && p.occ)
                         nd = occupied<FX>(p, c[kBX] + k * e[kBX], c[kBY] + k * e[kBY],
                                           c[kBZ] + k * e[kBZ]);
@@ -390,8 +406,8 @@ __device__ __forceinline__ unsigned long long march_tile(
                 if (nd) need |= 1u << k;
             }
         }
-        // --- A2: those (step, lane) lookups shared out over the warp, two per
-        //     lane at a time so that their record loads overlap (a3) -----------
+        // --- A2: those (step, lane) lookups shared out over the warp, one or two
+        //     per lane at a time (ViewBatch) so that their loads overlap (a3) ---
         unsigned nq = 0;
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
@@ -400,16 +416,21 @@ __device__ __forceinline__ unsigned long long march_tile(
             nq += __popc(m);
         }
         __syncwarp();
-        for (unsigned q = lane; q < nq; q += 64) {
-            // a lane without a second lookup repeats its first (same value, same entry)
-            const unsigned pa = ws.pairs[q], pb = ws.pairs[q + 32 < nq ? q + 32 : q];
-            uint32_t ca[kLatticeAxes], cq[kLatticeAxes];
-            const int32_t ha = step_coords(ws.c0, ws.e, pa & 31u, (uint32_t)i0 + (pa >> 5), ca);
-            const int32_t hb = step_coords(ws.c0, ws.e, pb & 31u, (uint32_t)i0 + (pb >> 5), cq);
-            const float ra = density<FX>(p, base, detail, weather, ca, ha);
-            const float rb = density<FX>(p, base, detail, weather, cq, hb);
-            ws.rho[pa >> 5][pa & 31u] = ra;
-            ws.rho[pb >> 5][pb & 31u] = rb;
+        constexpr int kViewBatch = ViewBatch<T>::value;
+        for (unsigned q = lane; q < nq; q += 32 * kViewBatch) {
+            // a lane without a further lookup repeats its first (same value, same entry)
+            unsigned pr[kViewBatch];
+            float rho[kViewBatch];
+#pragma unroll
+            for (int b = 0; b < kViewBatch; ++b) pr[b] = ws.pairs[q + 32 * b < nq ? q + 32 * b : q];
+#pragma unroll
+            for (int b = 0; b < kViewBatch; ++b) {
+                uint32_t cs[kLatticeAxes];
+                const int32_t hs = step_coords(ws.c0, ws.e, pr[b] & 31u, (uint32_t)i0 + (pr[b] >> 5), cs);
+                rho[b] = density<FX>(p, base, detail, weather, cs, hs);
+            }
+#pragma unroll
+            for (int b = 0; b < kViewBatch; ++b) ws.rho[pr[b] >> 5][pr[b] & 31u] = rho[b];
         }
         __syncwarp();
         // --- A3: each lane walks its steps in order: optical depth and the early

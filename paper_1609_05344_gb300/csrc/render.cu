@@ -159,10 +159,15 @@ std::mutex g_tune_mu;
 int g_best_config[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
 }  // namespace
 
+// Untuned default: shape 3 (8x16-pixel CTA of 4x8-pixel warps), 8 view steps
+// per warp iteration, the fastest for 8- and 16-step renders of every storage
+// precision measured.
+constexpr int kDefaultConfig = 3;
+
 int tuned_config(int precision, int light_steps) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int c = g_best_config[precision & 3][light_steps == 6 ? 1 : 0];
-    return c < 0 ? 0 : c;
+    return c < 0 ? kDefaultConfig : c;
 }
 void set_tuned_config(int precision, int light_steps, int config) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
