@@ -469,7 +469,8 @@ __device__ __forceinline__ unsigned long long march_tile(
             offs[k + 1] = offs[k] + __popc(m);
         }
         __syncwarp();
-        for (unsigned q = lane; q < offs[CH]; q += 32) {
+        const unsigned npairs = offs[CH];
+        for (unsigned q = lane; q < npairs; q += 32) {
             const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
             uint32_t cs[kLatticeAxes];
             const int32_t hs = step_coords(ws.c0, ws.e, ow, (uint32_t)(i0 + (int)k), cs);
