@@ -331,9 +331,15 @@ def run_gpu(args):
         return 2
 
     # untimed: the autotuner picks the launch configuration (tile shape, view
-    # steps per warp iteration) the frame loop then uses
-    tuned, tune_ms = api.autotune_render(vol, cam(0), prm, W, H, S, LS, jitter_frame=jit(0),
-                                         repeats=3)
+    # steps per warp iteration) the frame loop then uses, unless one is given
+    # (profiling runs pin it: under a profiler the tuner's timings are not the
+    # kernels' own)
+    if args.launch_config >= 0:
+        api.set_launch_config(args.precision, LS, args.launch_config)
+        tuned, tune_ms = args.launch_config, None
+    else:
+        tuned, tune_ms = api.autotune_render(vol, cam(0), prm, W, H, S, LS, jitter_frame=jit(0),
+                                             repeats=3)
     # clocks are sampled (every 200 ms) from the start of the warm-up through the
     # timed frames; warm-up continues, untimed, until the sampler is running
     clk = ClockSampler(local).__enter__()
@@ -962,6 +968,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "unorm16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch-config", type=int, default=-1,
+                    help="fast-1080p: pin the march launch configuration (0..7) instead of "
+                         "autotuning it")
     ap.add_argument("--no-extra-workloads", action="store_true",
                     help="fast-1080p only: skip the 64-view batch and serving summaries")
     ap.add_argument("--jitter", default="pixel", choices=["pixel", "frame", "none"],
