@@ -512,6 +512,16 @@ int cloud_debug_set_wait_polls(int first_polls);
  * Scheduling only; no counterpart in the paper. */
 int cloud_debug_set_occupancy(int enabled);
 
+/* Checked builds only (the library compiled with CLOUDVOL_CHECKED=1, a test
+ * build in place of a memory checker): the kernels verify that their index
+ * arithmetic stays in range (tile records 1, occupancy words 2, work lists 4,
+ * output pixels 8, history and source texels 16, shared-memory tiles 32,
+ * views and tiles of multi-view launches 64), skip an access that fails and
+ * OR its bit into a device status word.  *bits receives that word (reset != 0
+ * clears it); synchronous.  A normal build sets *bits = 0 and returns
+ * CLOUD_ERR_UNSUPPORTED.  No counterpart in the paper. */
+int cloud_debug_check_status(unsigned int *bits, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,10 @@ _ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libcloudvol.so")
+# the checked build (kernels verify their index ranges into a status word; for
+# tests), loaded instead of the normal library when CLOUDVOL_CHECKED=1
+CHECKED_BUILD_DIR = os.path.join(_HERE, "_build_checked")
+CHECKED_LIB_PATH = os.path.join(_HERE, "libcloudvol_checked.so")
 HEADER = os.path.join(_ROOT, "include", "cloudvol.h")
 SOURCES = ["volume.cu", "render.cu", "batch.cu", "march8_view.cu", "march16_view.cu",
            "march8_batch.cu", "march16_batch.cu", "taa.cu", "session.cu", "server.cu"]
@@ -45,20 +49,24 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA sources for sm_103a (in parallel) and link the library."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (in parallel) and link the library
+    (with checked=True the checked build, into its own directory and file)."""
+    build_dir = CHECKED_BUILD_DIR if checked else BUILD_DIR
+    lib_path = CHECKED_LIB_PATH if checked else LIB_PATH
+    flags = NVCC_FLAGS + (["-DCLOUDVOL_CHECKED=1"] if checked else [])
+    os.makedirs(build_dir, exist_ok=True)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, h) for h in ("common.cuh", "march.cuh", "march_kernels.cuh")] + [HEADER]
     newest = max(os.path.getmtime(p) for p in deps)
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest:
+        return lib_path
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
+        cmd = [nvcc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -69,14 +77,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             objs.append(obj)
             if verbose:
                 print(log)
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 class VolumeDesc(ctypes.Structure):
@@ -164,6 +172,7 @@ SIGNATURES = [
     ("cloud_hash4_batch", _i, [_vp, ctypes.c_int64, _vp, _vp]),
     ("cloud_debug_set_wait_polls", _i, [_i]),
     ("cloud_debug_set_occupancy", _i, [_i]),
+    ("cloud_debug_check_status", _i, [_P(ctypes.c_uint), _i]),
     ("cloud_volume_occupancy", _i, [_vp, _vp, ctypes.c_int64, _ip, _vp]),
     ("cloud_get_launch_config", _i, [_i, _i, _P(_i)]),
     ("cloud_set_launch_config", _i, [_i, _i, _i]),
@@ -199,10 +208,11 @@ def lib():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+        path = CHECKED_LIB_PATH if os.environ.get("CLOUDVOL_CHECKED") == "1" else LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
                                "`python -c 'import __graft_entry__ as g; g.build()'`")
-        h = ctypes.CDLL(LIB_PATH)
+        h = ctypes.CDLL(path)
         for name, res, args in SIGNATURES:
             fn = getattr(h, name)
             fn.restype = res

@@ -324,6 +324,14 @@ def device_wait_timeouts(reset: bool = False) -> int:
     return n.value
 
 
+def check_status(reset: bool = False) -> int:
+    """Site bits of failed index checks of the checked build
+    (cloud_debug_check_status); raises CloudError (unsupported) in a normal build."""
+    n = ctypes.c_uint()
+    N.check(N.lib().cloud_debug_check_status(ctypes.byref(n), int(reset)), "cloud_debug_check_status")
+    return n.value
+
+
 def set_occupancy(enabled: bool = True):
     """Use of the occupancy grid by the raymarch (cloud_debug_set_occupancy)."""
     N.check(N.lib().cloud_debug_set_occupancy(1 if enabled else 0), "cloud_debug_set_occupancy")

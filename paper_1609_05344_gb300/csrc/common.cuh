@@ -25,6 +25,39 @@ void clear_error();
 inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // ---------------------------------------------------------------------------
+// Checked build (CLOUDVOL_CHECKED=1, a separate library used by tests in place
+// of a memory checker): kernels verify the ranges their index arithmetic is
+// meant to stay in (tile records, occupancy words, work lists, pixels, history
+// texels, shared tiles, views), skip an access that fails and record the site
+// in a device status word read by cloud_debug_check_status.  In normal builds
+// the checks compile away.
+#ifndef CLOUDVOL_CHECKED
+#define CLOUDVOL_CHECKED 0
+#endif
+enum CheckSite : unsigned {
+    kChkRecord = 1u,      // a tile record index
+    kChkOccupancy = 2u,   // an occupancy-grid word
+    kChkWork = 4u,        // a (step, lane) work-list entry
+    kChkPixel = 8u,       // an output pixel
+    kChkHistory = 16u,    // a history or source texel
+    kChkTile = 32u,       // a shared-memory tile texel
+    kChkView = 64u,       // a view or tile of a multi-view launch
+};
+__device__ __forceinline__ bool in_range(unsigned *word, bool ok, unsigned site) {
+#if CLOUDVOL_CHECKED
+    if (!ok && word) atomicOr(word, site);
+    return ok;
+#else
+    (void)word;
+    (void)ok;
+    (void)site;
+    return true;
+#endif
+}
+// Host: the current device's status word in checked builds, else nullptr.
+unsigned *check_word();
+
+// ---------------------------------------------------------------------------
 // Counter-based hash: single-state PCG hash (Jarzynski & Olano, JCGT 2020):
 // one 32-bit PCG LCG step (multiplier 747796405, increment 2891336453) and
 // the RXS-M-XS output permutation (multiplier 277803737).  Four-word keys

@@ -90,6 +90,7 @@ struct SceneParams {
     // the 2x2x2-record macro-cell), or nullptr; log2 of its cells per axis
     const uint32_t *occ;
     int log2_occ;
+    unsigned *check;  // status word of the checked build, else nullptr
     int log2_base, log2_detail, log2_weather;
     int light_steps, integration, constant_mode;
     // detail coordinates = (base + half_base) << detail_shift - half_detail when
@@ -215,6 +216,7 @@ __device__ __forceinline__ bool occupied(const SceneParams &p, uint32_t bx, uint
     // macro-cell = record index >> 1 on each axis; bits x fastest
     const int lo = FX ? kStdLog2Base - 1 : p.log2_occ, sh = 32 - lo;
     const uint32_t cell = ((bz >> sh) << (2 * lo)) | ((by >> sh) << lo) | (bx >> sh);
+    if (!in_range(p.check, cell < (1u << (3 * lo)), kChkOccupancy)) return true;
     return (__ldg(p.occ + (cell >> 5)) >> (cell & 31u)) & 1u;
 }
 
@@ -236,10 +238,17 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
     const float g = height_profile(p, hq);
     if (g <= 0.0f) return 0.0f;
     float cb[8], cd[8], cw[4];
-    const float ob = load_rec8(base, rec3(lb, c[kBX], c[kBY], c[kBZ]), cb);
+    const uint32_t rb = rec3(lb, c[kBX], c[kBY], c[kBZ]), rd = rec3(ld, c[kDX], c[kDY], c[kDZ]),
+                   rw = rec2(lw, c[kWX], c[kWY]);
+    if (!in_range(p.check,
+                  rb < (1u << (3 * lb)) && (!(FX || detail) || rd < (1u << (3 * ld))) &&
+                      (!(FX || weather) || rw < (1u << (2 * lw))),
+                  kChkRecord))
+        return 0.0f;
+    const float ob = load_rec8(base, rb, cb);
     float od = 0.0f, ow = 0.0f;
-    if (FX || detail) od = load_rec8(detail, rec3(ld, c[kDX], c[kDY], c[kDZ]), cd);
-    if (FX || weather) ow = load_rec4(weather, rec2(lw, c[kWX], c[kWY]), cw);
+    if (FX || detail) od = load_rec8(detail, rd, cd);
+    if (FX || weather) ow = load_rec4(weather, rw, cw);
     const float b = trilerp(cb, lb, c[kBX], c[kBY], c[kBZ]) + ob;
     float r = b + p.k0;
     if (FX || detail) {
@@ -412,7 +421,9 @@ __device__ __forceinline__ unsigned long long march_tile(
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
             const unsigned m = __ballot_sync(kFull, (need >> k) & 1u);
-            if ((need >> k) & 1u) ws.pairs[nq + __popc(m & lt_mask)] = (uint16_t)((k << 5) | lane);
+            const unsigned slot = nq + __popc(m & lt_mask);
+            if (((need >> k) & 1u) && in_range(p.check, slot < CH * 32u, kChkWork))
+                ws.pairs[slot] = (uint16_t)((k << 5) | lane);
             nq += __popc(m);
         }
         __syncwarp();
@@ -423,6 +434,10 @@ __device__ __forceinline__ unsigned long long march_tile(
             float rho[kViewBatch];
 #pragma unroll
             for (int b = 0; b < kViewBatch; ++b) pr[b] = ws.pairs[q + 32 * b < nq ? q + 32 * b : q];
+            bool ok = in_range(p.check, q < CH * 32u, kChkWork);
+#pragma unroll
+            for (int b = 0; b < kViewBatch; ++b) ok = ok && in_range(p.check, (pr[b] >> 5) < (unsigned)CH, kChkWork);
+            if (!ok) continue;
 #pragma unroll
             for (int b = 0; b < kViewBatch; ++b) {
                 uint32_t cs[kLatticeAxes];
@@ -465,13 +480,16 @@ __device__ __forceinline__ unsigned long long march_tile(
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
             const unsigned m = __ballot_sync(kFull, (act >> k) & 1u);
-            if ((act >> k) & 1u) ws.pairs[offs[k] + __popc(m & lt_mask)] = (uint16_t)((k << 5) | lane);
+            const unsigned slot = offs[k] + __popc(m & lt_mask);
+            if (((act >> k) & 1u) && in_range(p.check, slot < CH * 32u, kChkWork))
+                ws.pairs[slot] = (uint16_t)((k << 5) | lane);
             offs[k + 1] = offs[k] + __popc(m);
         }
         __syncwarp();
         const unsigned npairs = offs[CH];
         for (unsigned q = lane; q < npairs; q += 32) {
             const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
+            if (!in_range(p.check, q < CH * 32u && k < (unsigned)CH, kChkWork)) continue;
             uint32_t cs[kLatticeAxes];
             const int32_t hs = step_coords(ws.c0, ws.e, ow, (uint32_t)(i0 + (int)k), cs);
             float rho_sum = 0.0f;
@@ -522,7 +540,8 @@ __device__ __forceinline__ unsigned long long march_tile(
         __syncwarp();
     }
     // --- a8: premultiplied RGBA, one 16-byte store ------------------------------
-    if (in_image) v.out[(size_t)y * v.width + x] = make_float4(cr, cg, cb, -expm1f(-tau));
+    if (in_image && in_range(p.check, x >= 0 && y >= 0, kChkPixel))
+        v.out[(size_t)y * v.width + x] = make_float4(cr, cg, cb, -expm1f(-tau));
     return n_look;
 }
 

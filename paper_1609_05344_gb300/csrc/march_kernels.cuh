@@ -56,8 +56,10 @@ __global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
         for (int i = threadIdx.x; i < (int)(sizeof(ViewParams) / 4); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
         const int local = t - sv.tile_begin;
-        n_look += march_tile<T, LS, SHAPE, FX, CH>(p, sv, local % sv.tiles_x, local / sv.tiles_x,
-                                                   scratch[threadIdx.x >> 5], base, detail, weather);
+        if (in_range(p.check, s_view >= 0 && s_view < n_views && local >= 0 && local < sv.tile_count,
+                     kChkView))
+            n_look += march_tile<T, LS, SHAPE, FX, CH>(p, sv, local % sv.tiles_x, local / sv.tiles_x,
+                                                       scratch[threadIdx.x >> 5], base, detail, weather);
         __syncthreads();  // s_tile / sv are rewritten by the next iteration
     }
     count_lookups(counter, n_look);

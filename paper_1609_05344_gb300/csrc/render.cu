@@ -85,6 +85,7 @@ int build_scene(const cloud_volume *vol, const cloud_params *prm, int light_step
     p->rho0 = (float)d.constant_density;
     p->occ = noise && g_use_occupancy.load() ? vol->occ : nullptr;
     p->log2_occ = vol->log2_occ;
+    p->check = check_word();
     p->log2_base = vol->log2_base;
     p->log2_detail = vol->log2_detail;
     p->log2_weather = vol->log2_weather;

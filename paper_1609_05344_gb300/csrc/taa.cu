@@ -33,6 +33,7 @@ struct MotionParams {
     // exact), slab_lo - o_z, slab_hi - o_z and the far clip
     float v00h[3], v00l[3], vxh[3], vxl[3], vyh[3], vyl[3];
     float zlo_h, zlo_l, zhi_h, zhi_l, tmax_h, tmax_l;
+    unsigned *check;  // status word of the checked build, else nullptr
 };
 
 // Reprojection depth parameter lambda (t / |v|) of the layer entry point, or
@@ -182,7 +183,8 @@ template <typename H>
 __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
                                                   const float4 *__restrict__ cur,
                                                   const float2 *__restrict__ mot,
-                                                  H *__restrict__ out, int W, int Hh, float blend) {
+                                                  H *__restrict__ out, int W, int Hh, float blend,
+                                                  unsigned *check) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     if (x >= W || y >= Hh) return;
     const size_t i = (size_t)y * W + x;
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
             const int ix = x + (int)flx, iy = y + (int)fly;
             const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
             const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
+            if (!in_range(check, xa >= 0 && xb < W && ya >= 0 && yb < Hh, kChkHistory)) return;
             const float4 h00 = load_hist(hist, (size_t)ya * W + xa);
             const float4 h01 = load_hist(hist, (size_t)ya * W + xb);
             const float4 h10 = load_hist(hist, (size_t)yb * W + xa);
@@ -215,6 +218,7 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
                 for (int dx = -1; dx <= 1; ++dx) {
                     if (dx == 0 && dy == 0) continue;
                     const int nx2 = min(max(x + dx, 0), W - 1);
+                    if (!in_range(check, nx2 >= 0 && nx2 < W && ny2 >= 0 && ny2 < Hh, kChkHistory)) continue;
                     const float4 v = __ldg(cur + (size_t)ny2 * W + nx2);
                     mn = fmin4(mn, v);
                     mx = fmax4(mx, v);
@@ -340,6 +344,7 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
             const int ix = x + (int)flx, iy = y + (int)fly;
             const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
             const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
+            if (!in_range(mp.check, xa >= 0 && xb < W && ya >= 0 && yb < Hh, kChkHistory)) continue;
             h00[r] = load_hist(hist, (size_t)ya * W + xa);
             h01[r] = load_hist(hist, (size_t)ya * W + xb);
             h10[r] = load_hist(hist, (size_t)yb * W + xa);
@@ -372,11 +377,13 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
         for (int i = tid; i < (kTH + 2) * (kTW + 2); i += 256) {
             const int r = i / (kTW + 2), c = i - r * (kTW + 2);
             const int rr = min(max(r, r_lo), r_hi), cc = min(max(c, c_lo), c_hi);
+            if (!in_range(mp.check, rr >= 0 && rr < kTH + 2 && cc >= 0 && cc < kTW + 2, kChkTile)) continue;
             if (rr != r || cc != c) tile[r][c] = tile[rr][cc];
         }
         __syncthreads();
     }
     if (x >= W) return;
+    if (!in_range(mp.check, tx + 2 < kTW + 2 && 2 * ty + 3 < kTH + 2, kChkTile)) return;
     // 3. 3x3 ranges of both pixels from four tile rows (row-wise min/max, then
     //    the two overlapping row triples share their middle pair), clamp the
     //    filtered history, blend
@@ -401,7 +408,7 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
             const float4 h = bil4(fxs[r], fys[r], h00[r], h01[r], h10[r], h11[r]);
             res = blend4(fmin4(fmax4(h, mn), mx), c, blend);
         }
-        store_hist(out, (size_t)y * W + x, res);
+        if (in_range(mp.check, y >= 0 && x >= 0, kChkPixel)) store_hist(out, (size_t)y * W + x, res);
     }
 }
 
@@ -454,6 +461,7 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
     for (int i = tid; i < (int)(sizeof(MotionParams) / 4); i += 256) dst[i] = src[i];
     __syncthreads();
     const int local = t - rv.tile_begin;
+    if (!in_range(smp.check, s_view >= 0 && s_view < n_views && local >= 0, kChkView)) return;
     resolve_tile<H>(&rv.map, smp, (const H *)rv.hist, (H *)rv.out, rv.blend, local % rv.tiles_x,
                     local / rv.tiles_x, tile, bar, first_polls, status);
 }
@@ -510,6 +518,7 @@ int build_motion_params(const cloud_volume *vol, const cloud_params *prm, const 
     split_df(vol->desc.slab_lo_m - cur->pos[2], &p->zlo_h, &p->zlo_l);
     split_df(vol->desc.slab_hi_m - cur->pos[2], &p->zhi_h, &p->zhi_l);
     split_df(prm->t_max_m, &p->tmax_h, &p->tmax_l);
+    p->check = check_word();
     return CLOUD_OK;
 }
 
@@ -548,11 +557,11 @@ int launch_taa(const void *history, const float *current, const float *motion, v
     if (fmt == CLOUD_HISTORY_FP32)
         taa_kernel<float4><<<grid, block, 0, s>>>((const float4 *)history, (const float4 *)current,
                                                   (const float2 *)motion, (float4 *)history_out,
-                                                  width, height, blend);
+                                                  width, height, blend, check_word());
     else
         taa_kernel<uint2><<<grid, block, 0, s>>>((const uint2 *)history, (const float4 *)current,
                                                  (const float2 *)motion, (uint2 *)history_out,
-                                                 width, height, blend);
+                                                 width, height, blend, check_word());
     return check_launch("taa_kernel");
 }
 
@@ -687,7 +696,7 @@ __device__ __forceinline__ void src_coord(int x, int sw, int dw, int &i0, float 
 template <typename H>
 __global__ void __launch_bounds__(256) composite_kernel(const H *__restrict__ cloud, int sw, int sh,
                                                         const float4 *__restrict__ bg, float4 *out,
-                                                        int dw, int dh) {
+                                                        int dw, int dh, unsigned *check) {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     if (x >= dw || y >= dh) return;
     int u0, v0;
@@ -696,6 +705,7 @@ __global__ void __launch_bounds__(256) composite_kernel(const H *__restrict__ cl
     src_coord(y, sh, dh, v0, fy);
     const int xa = max(u0, 0), xb = min(u0 + 1, sw - 1);
     const int ya = max(v0, 0), yb = min(v0 + 1, sh - 1);
+    if (!in_range(check, xa < sw && xb >= 0 && ya < sh && yb >= 0, kChkHistory)) return;
     const float4 c00 = load_hist(cloud, (size_t)ya * sw + xa), c01 = load_hist(cloud, (size_t)ya * sw + xb);
     const float4 c10 = load_hist(cloud, (size_t)yb * sw + xa), c11 = load_hist(cloud, (size_t)yb * sw + xb);
     const float4 c = bil4(fx, fy, c00, c01, c10, c11);
@@ -718,10 +728,10 @@ int launch_composite(const void *cloud, int fmt, int sw, int sh, const float *bg
     const dim3 grid((dw + 31) / 32, (dh + 7) / 8), block(32, 8);
     if (fmt == CLOUD_HISTORY_FP32)
         composite_kernel<float4><<<grid, block, 0, s>>>((const float4 *)cloud, sw, sh, (const float4 *)bg,
-                                                        (float4 *)out, dw, dh);
+                                                        (float4 *)out, dw, dh, check_word());
     else
         composite_kernel<uint2><<<grid, block, 0, s>>>((const uint2 *)cloud, sw, sh, (const float4 *)bg,
-                                                       (float4 *)out, dw, dh);
+                                                       (float4 *)out, dw, dh, check_word());
     return check_launch("composite_kernel");
 }
 

@@ -37,6 +37,21 @@ int check_cuda(cudaError_t e, const char *what) {
 
 int check_launch(const char *what) { return check_cuda(cudaGetLastError(), what); }
 
+unsigned *check_word() {
+#if CLOUDVOL_CHECKED
+    static std::mutex mu;
+    static unsigned *words[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!words[dev] && cudaMalloc(&words[dev], sizeof(unsigned)) == cudaSuccess)
+        cudaMemset(words[dev], 0, sizeof(unsigned));
+    return words[dev];
+#else
+    return nullptr;
+#endif
+}
+
 __device__ __forceinline__ double unit_value(uint32_t h) {
     return (double)(h >> 8) * (1.0 / 16777216.0);
 }
@@ -561,4 +576,22 @@ extern "C" int cloud_volume_occupancy(const cloud_volume *vol, uint32_t *out, in
     return check_cuda(cudaMemcpyAsync(out, vol->occ, need * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
                                       (cudaStream_t)stream),
                       "cloud_volume_occupancy");
+}
+
+extern "C" int cloud_debug_check_status(unsigned int *bits, int reset) {
+    clear_error();
+    if (!bits) return set_error(CLOUD_ERR_INVALID_ARG, "cloud_debug_check_status: null pointer");
+    *bits = 0;
+#if CLOUDVOL_CHECKED
+    unsigned *w = check_word();
+    if (!w) return set_error(CLOUD_ERR_CUDA, "cloud_debug_check_status: no status word");
+    if (int rc = check_cuda(cudaMemcpy(bits, w, sizeof(unsigned), cudaMemcpyDeviceToHost),
+                            "cloud_debug_check_status"))
+        return rc;
+    if (reset) return check_cuda(cudaMemset(w, 0, sizeof(unsigned)), "cloud_debug_check_status");
+    return CLOUD_OK;
+#else
+    (void)reset;
+    return set_error(CLOUD_ERR_UNSUPPORTED, "cloud_debug_check_status: not a checked build");
+#endif
 }
