@@ -158,6 +158,24 @@ __device__ __forceinline__ float4 fmin4(float4 a, float4 b) {
 __device__ __forceinline__ float4 fmax4(float4 a, float4 b) {
     return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
 }
+// Three-input minimum / maximum (sm_100+ PTX min/max with three sources),
+// per channel; exact, like every min/max.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float4 min3_4(float4 a, float4 b, float4 c) {
+    return make_float4(min3f(a.x, b.x, c.x), min3f(a.y, b.y, c.y), min3f(a.z, b.z, c.z), min3f(a.w, b.w, c.w));
+}
+__device__ __forceinline__ float4 max3_4(float4 a, float4 b, float4 c) {
+    return make_float4(max3f(a.x, b.x, c.x), max3f(a.y, b.y, c.y), max3f(a.z, b.z, c.z), max3f(a.w, b.w, c.w));
+}
 // a + t (b - a) on packed FP32x2 lanes (each lane rounds like the scalar form)
 __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t) {
     return __ffma2_rn(make_float2(t, t), __fadd2_rn(b, make_float2(-a.x, -a.y)), a);
@@ -296,12 +314,12 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
     //    The box starts at texel (x0 - 1, y0 - 1): its x offset in bytes is
     //    16 (x0 - 1), a multiple of 16; texels outside the frame arrive as
     //    zeros and are replaced by their clamped neighbours below.
+    //    Thread 0 initialises the barrier and issues the copy; the other
+    //    threads only touch the barrier after the __syncthreads below, so the
+    //    motion arithmetic starts at once.
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
         constexpr unsigned kTileBytes = (kTH + 2) * (kTW + 2) * 16;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                      ::"r"(smem_addr(&bar)), "r"(kTileBytes) : "memory");
@@ -352,6 +370,7 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
             use[r] = true;
         }
     }
+    __syncthreads();  // the barrier's initialisation is visible to every thread
     const bool landed = mbar_wait(&bar, 0, first_polls);
     if (!__syncthreads_and(landed)) {
         // the copy did not complete within the bounded wait: count it (globally
@@ -384,15 +403,15 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
     }
     if (x >= W) return;
     if (!in_range(mp.check, tx + 2 < kTW + 2 && 2 * ty + 3 < kTH + 2, kChkTile)) return;
-    // 3. 3x3 ranges of both pixels from four tile rows (row-wise min/max, then
-    //    the two overlapping row triples share their middle pair), clamp the
-    //    filtered history, blend
-    float4 mn12, mx12;
+    // 3. 3x3 ranges of both pixels from four tile rows (three-input min/max):
+    //    the two rows both windows share are reduced once, each pixel adds
+    //    its own third row; clamp the filtered history, blend
+    float4 mn12, mx12;  // rows 2 ty + 1 and 2 ty + 2, shared by both pixels
     {
         const float4 a1 = tile[2 * ty + 1][tx], b1 = tile[2 * ty + 1][tx + 1], c1 = tile[2 * ty + 1][tx + 2];
         const float4 a2 = tile[2 * ty + 2][tx], b2 = tile[2 * ty + 2][tx + 1], c2 = tile[2 * ty + 2][tx + 2];
-        mn12 = fmin4(fmin4(fmin4(a1, b1), c1), fmin4(fmin4(a2, b2), c2));
-        mx12 = fmax4(fmax4(fmax4(a1, b1), c1), fmax4(fmax4(a2, b2), c2));
+        mn12 = fmin4(min3_4(a1, b1, c1), min3_4(a2, b2, c2));
+        mx12 = fmax4(max3_4(a1, b1, c1), max3_4(a2, b2, c2));
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -403,8 +422,8 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
         if (use[r]) {
             const int k = 2 * ty + 3 * r;  // the row of the pair's window not shared
             const float4 a = tile[k][tx], b = tile[k][tx + 1], d = tile[k][tx + 2];
-            const float4 mn = fmin4(mn12, fmin4(fmin4(a, b), d));
-            const float4 mx = fmax4(mx12, fmax4(fmax4(a, b), d));
+            const float4 mn = min3_4(mn12, a, min3_4(b, d, b));
+            const float4 mx = max3_4(mx12, a, max3_4(b, d, b));
             const float4 h = bil4(fxs[r], fys[r], h00[r], h01[r], h10[r], h11[r]);
             res = blend4(fmin4(fmax4(h, mn), mx), c, blend);
         }
