@@ -200,8 +200,9 @@ int cloud_volume_export(const cloud_volume *vol, float *base, float *detail, flo
                         void *stream);
 
 /* Copies the volume's occupancy grid into `out` (device, `words` uint32,
- * caller-owned): one bit per macro-cell of 2 x 2 x 2 base-tile texel cells,
- * 2^(3 * *log2_cells) cells with x fastest, bit i of word i / 32 for cell i.
+ * caller-owned): one bit per cell of the base tile's texel lattice (the
+ * footprint of one trilinear record), 2^(3 * *log2_cells) cells with x
+ * fastest, bit i of word i / 32 for cell i.
  * A clear bit means the density is provably zero for every sample whose base
  * record lies in the cell (the bound max B - detail_weight min Dt - coverage
  * < 0 over its records); the raymarch then skips that lookup's memory reads,

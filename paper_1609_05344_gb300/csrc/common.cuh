@@ -95,10 +95,10 @@ struct cloud_volume {
     void *base;      // device, base_n^3 corner-packed records of the storage precision
     void *detail;    // device or nullptr (detail_n^3 records)
     void *weather;   // device or nullptr (weather_n^2 records)
-    // occupancy grid: one bit per macro-cell of 2x2x2 base records (x fastest),
+    // occupancy grid: one bit per cell of 2^kOccShift base records per axis (x fastest),
     // clear where the density is provably 0 throughout (see build_occupancy)
     uint32_t *occ;   // device or nullptr (constant density)
-    int log2_occ;    // macro-cells per axis = 2^log2_occ = base_n / 2
+    int log2_occ;    // macro-cells per axis = 2^log2_occ = base_n / 2^kOccShift
     int device;
 };
 
@@ -111,6 +111,12 @@ inline int ilog2(int n) {
 }
 
 inline size_t precision_bytes(int p) { return p == CLOUD_PRECISION_FP32 ? 4 : 2; }
+
+// Occupancy grid cell: 2^kOccShift base records per axis.
+#ifndef CLOUDVOL_OCC_SHIFT
+#define CLOUDVOL_OCC_SHIFT 0
+#endif
+constexpr int kOccShift = CLOUDVOL_OCC_SHIFT;
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, about

@@ -87,7 +87,8 @@ struct SceneParams {
     // k0 - b + w_d b; w_off = 1/2 - b (weather values are stored centred)
     float k0, inv_1mc, detail_w, rho0, w_off;
     // occupancy grid of the volume (bit set: density may be > 0 somewhere in
-    // the 2x2x2-record macro-cell), or nullptr; log2 of its cells per axis
+    // the macro-cell of 2^kOccShift records per axis), or nullptr; log2 of its
+    // cells per axis
     const uint32_t *occ;
     int log2_occ;
     unsigned *check;  // status word of the checked build, else nullptr
@@ -213,8 +214,8 @@ __device__ __forceinline__ float height_profile(const SceneParams &p, int32_t hq
 // the volume's bound proves B - w_d Dt - c < 0, i.e. zero density.
 template <bool FX>
 __device__ __forceinline__ bool occupied(const SceneParams &p, uint32_t bx, uint32_t by, uint32_t bz) {
-    // macro-cell = record index >> 1 on each axis; bits x fastest
-    const int lo = FX ? kStdLog2Base - 1 : p.log2_occ, sh = 32 - lo;
+    // macro-cell = record index >> kOccShift on each axis; bits x fastest
+    const int lo = FX ? kStdLog2Base - kOccShift : p.log2_occ, sh = 32 - lo;
     const uint32_t cell = ((bz >> sh) << (2 * lo)) | ((by >> sh) << lo) | (bx >> sh);
     if (!in_range(p.check, cell < (1u << (3 * lo)), kChkOccupancy)) return true;
     return (__ldg(p.occ + (cell >> 5)) >> (cell & 31u)) & 1u;

@@ -243,8 +243,8 @@ __device__ __forceinline__ void record_range(const T *tile, uint32_t rec, float 
     }
 }
 
-// Occupancy grid.  Macro-cell (X, Y, Z) covers the base records 2X..2X+1 on
-// each axis, i.e. every sample whose base record lies there.  Its bit is
+// Occupancy grid.  Macro-cell (X, Y, Z) covers the base records mX..mX+m-1 on
+// each axis (m = 2^kOccShift), i.e. every sample whose base record lies there.  Its bit is
 // clear when, for every such sample,
 //   B - w_d Dt - c <= max B - w_d min Dt - c < 0      (w_d >= 0; max Dt if < 0)
 // with max B over the corners of those base records and the Dt extreme over
@@ -258,7 +258,7 @@ template <typename T>
 __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T *__restrict__ detail,
                                  int log2d, double ratio, float dt_all_lo, float dt_all_hi,
                                  float k0, float wd, uint32_t *__restrict__ occ) {
-    const int lo2 = log2b - 1;
+    const int lo2 = log2b - kOccShift;
     const uint32_t M = 1u << lo2, nb = 1u << log2b, nd = 1u << log2d;
     const uint32_t total = M * M * M;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (total + 31) / 32;
@@ -267,24 +267,25 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
         for (uint32_t b = 0; b < 32 && 32 * w + b < total; ++b) {
             const uint32_t cell = 32 * w + b;
             const uint32_t X = cell & (M - 1), Y = (cell >> lo2) & (M - 1), Z = cell >> (2 * lo2);
+            constexpr uint32_t m = 1u << kOccShift;  // base records per cell and axis
             float bmax = -INFINITY;
-            for (uint32_t dz = 0; dz < 2; ++dz)
-                for (uint32_t dy = 0; dy < 2; ++dy)
-                    for (uint32_t dx = 0; dx < 2; ++dx) {
+            for (uint32_t dz = 0; dz < m; ++dz)
+                for (uint32_t dy = 0; dy < m; ++dy)
+                    for (uint32_t dx = 0; dx < m; ++dx) {
                         float l, h;
-                        record_range(base, (((2 * Z + dz) << (2 * log2b)) | ((2 * Y + dy) << log2b) |
-                                            (2 * X + dx)), l, h);
+                        record_range(base, (((m * Z + dz) << (2 * log2b)) | ((m * Y + dy) << log2b) |
+                                            (m * X + dx)), l, h);
                         bmax = fmaxf(bmax, h);
                     }
             float dlo = dt_all_lo, dhi = dt_all_hi;
             if (detail && ratio > 0.0) {
                 // detail record range along each axis: samples with base texel-centre
-                // coordinate s in [2K, 2K + 2) have detail coordinate (s + 1/2) ratio - 1/2
+                // coordinate s in [m K, m K + m) have detail coordinate (s + 1/2) ratio - 1/2
                 const uint32_t K[3] = {X, Y, Z};
                 int r0[3], r1[3];
                 for (int a = 0; a < 3; ++a) {
-                    r0[a] = (int)floor((2.0 * K[a] + 0.5) * ratio - 0.5);
-                    r1[a] = (int)floor((2.0 * K[a] + 2.5) * ratio - 0.5);
+                    r0[a] = (int)floor(((double)m * K[a] + 0.5) * ratio - 0.5);
+                    r1[a] = (int)floor(((double)m * K[a] + m + 0.5) * ratio - 0.5);
                 }
                 dlo = INFINITY;
                 dhi = -INFINITY;
@@ -358,7 +359,7 @@ unsigned grid_for(uint64_t n, unsigned block) {
 template <typename T>
 int build_occupancy(cloud_volume *v, cudaStream_t s) {
     const cloud_volume_desc &d = v->desc;
-    v->log2_occ = v->log2_base - 1;
+    v->log2_occ = v->log2_base - kOccShift;
     const uint64_t cells = 1ull << (3 * v->log2_occ), words = (cells + 31) / 32;
     if (int rc = check_cuda(cudaMalloc(&v->occ, words * sizeof(uint32_t)), "cudaMalloc occupancy"))
         return rc;

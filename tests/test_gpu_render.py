@@ -181,29 +181,33 @@ def test_occupancy_grid_is_conservative(api, oracle):
     ov = oracle.Volume(desc)
     B, Dt = ov.base, ov.detail
     nb, nd = B.shape[0], Dt.shape[0]
-    assert occ.shape == (nb // 2,) * 3
-    Bp = np.pad(B, ((0, 2), (0, 2), (0, 2)), mode="wrap")
+    m = nb // occ.shape[0]  # base records per cell and axis
+    assert occ.shape == (nb // m,) * 3 and m in (1, 2)
+    Bp = np.pad(B, ((0, m), (0, m), (0, m)), mode="wrap")
     bmax = np.full(occ.shape, -np.inf)
-    for dz in range(3):
-        for dy in range(3):
-            for dx in range(3):
-                bmax = np.maximum(bmax, Bp[dz:dz + nb:2, dy:dy + nb:2, dx:dx + nb:2])
-    # detail texels of base macro-cell K (base texels 2K..2K+2 at 2 detail texels each,
-    # base period = 8 detail periods): detail texels 4K .. 4K+5 (mod nd)
+    for dz in range(m + 1):
+        for dy in range(m + 1):
+            for dx in range(m + 1):
+                bmax = np.maximum(bmax, Bp[dz:dz + nb:m, dy:dy + nb:m, dx:dx + nb:m])
+    # detail texels of base cell K (base texels mK..mK+m at 2 detail texels each,
+    # base period = 8 detail periods): detail texels 2mK .. 2mK+2m+1 (mod nd)
     ratio = desc["base_period"] / desc["detail_period"] * nd / nb
     assert ratio == 2.0
-    Dp = np.pad(Dt, ((0, 6), (0, 6), (0, 6)), mode="wrap")
-    dmin = np.full((nd // 4,) * 3, np.inf)
-    for dz in range(6):
-        for dy in range(6):
-            for dx in range(6):
-                dmin = np.minimum(dmin, Dp[dz:dz + nd:4, dy:dy + nd:4, dx:dx + nd:4])
-    k = np.arange(nb // 2) % (nd // 4)
+    w = 2 * m + 2
+    Dp = np.pad(Dt, ((0, w), (0, w), (0, w)), mode="wrap")
+    dmin = np.full((nd // (2 * m),) * 3, np.inf)
+    for dz in range(w):
+        for dy in range(w):
+            for dx in range(w):
+                dmin = np.minimum(dmin, Dp[dz:dz + nd:2 * m, dy:dy + nd:2 * m, dx:dx + nd:2 * m])
+    k = np.arange(nb // m) % (nd // (2 * m))
     dmin_cells = dmin[np.ix_(k, k, k)]
     bound = bmax - desc["detail_weight"] * dmin_cells - desc["coverage"]
     empty = ~occ
     assert empty.mean() > 0.2
     assert bound[empty].max() < 0.0
+
+
 def test_reference_720p_sampled(api, oracle):
     wl = I.workload("reference")
     err, _ = _sampled(api, oracle, wl, I.ground_camera(), -1, 4000, 9)
