@@ -259,7 +259,7 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
                                  int log2d, double ratio, float dt_all_lo, float dt_all_hi,
                                  float k0, float wd, uint32_t *__restrict__ occ) {
     const int lo2 = log2b - kOccShift;
-    const uint32_t M = 1u << lo2, nb = 1u << log2b, nd = 1u << log2d;
+    const uint32_t M = 1u << lo2, nd = 1u << log2d;
     const uint32_t total = M * M * M;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (total + 31) / 32;
          w += gridDim.x * blockDim.x) {
@@ -306,7 +306,6 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
         }
         occ[w] = bits;
     }
-    (void)nb;
 }
 
 // Extremes of the corners of every record of a tile (for occupancy bounds
