@@ -200,12 +200,12 @@ int cloud_volume_export(const cloud_volume *vol, float *base, float *detail, flo
                         void *stream);
 
 /* Copies the volume's occupancy grid into `out` (device, `words` uint32,
- * caller-owned): one bit per cell of the base tile's texel lattice (the
- * footprint of one trilinear record), 2^(3 * *log2_cells) cells with x
- * fastest, bit i of word i / 32 for cell i.
- * A clear bit means the density is provably zero for every sample whose base
- * record lies in the cell (the bound max B - detail_weight min Dt - coverage
- * < 0 over its records); the raymarch then skips that lookup's memory reads,
+ * caller-owned): one bit per cell of half a base-tile texel on each axis
+ * (8 per trilinear record), 2^(3 * *log2_cells) cells with x fastest, bit i
+ * of word i / 32 for cell i.
+ * A clear bit means the density is provably zero for every sample in the cell
+ * (max B - detail_weight min Dt - coverage < 0, with the exact extremes of the
+ * interpolated tiles over the cell); the raymarch then skips that lookup's memory reads,
  * which changes no result.  With out == NULL only *log2_cells is set (-1 for
  * a constant-density volume, which has no grid).  words must be
  * ceil(2^(3 * *log2_cells) / 32).  For tests and tools.

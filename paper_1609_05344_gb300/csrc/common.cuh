@@ -114,7 +114,7 @@ inline size_t precision_bytes(int p) { return p == CLOUD_PRECISION_FP32 ? 4 : 2;
 
 // Occupancy grid cell: 2^kOccShift base records per axis.
 #ifndef CLOUDVOL_OCC_SHIFT
-#define CLOUDVOL_OCC_SHIFT 0
+#define CLOUDVOL_OCC_SHIFT -1
 #endif
 constexpr int kOccShift = CLOUDVOL_OCC_SHIFT;
 

@@ -231,16 +231,33 @@ __global__ void decode_kernel(const T *__restrict__ packed, int stride, float *_
 // FP32 records the dx = 1 corners are the dx = 0 corners plus the stored
 // differences).  Rounding of the lerps is covered by the caller's margin.
 template <typename T>
-__device__ __forceinline__ void record_range(const T *tile, uint32_t rec, float &lo, float &hi) {
+__device__ __forceinline__ void record_corners(const T *tile, uint32_t rec, float v[8]) {
     float c[8];
     const float off = load_rec8(tile, rec, c) - texel_bias<T>();
-    float v[8] = {c[0], c[1], c[2], c[3], c[0] + c[4], c[1] + c[5], c[2] + c[6], c[3] + c[7]};
-    lo = hi = v[0] + off;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        v[r] = c[r] + off;
+        v[r + 4] = (c[r] + c[r + 4]) + off;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void record_range(const T *tile, uint32_t rec, float &lo, float &hi) {
+    float v[8];
+    record_corners(tile, rec, v);
+    lo = hi = v[0];
 #pragma unroll
     for (int r = 1; r < 8; ++r) {
-        lo = fminf(lo, v[r] + off);
-        hi = fmaxf(hi, v[r] + off);
+        lo = fminf(lo, v[r]);
+        hi = fmaxf(hi, v[r]);
     }
+}
+// Trilinear value of a record's corners (r = 4 dx + 2 dy + dz) at fractions f.
+__device__ __forceinline__ float trilinear_at(const float v[8], float fx, float fy, float fz) {
+    float yz[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) yz[r] = fmaf(fx, v[r + 4] - v[r], v[r]);  // (dy, dz) pairs
+    const float z0 = fmaf(fy, yz[2] - yz[0], yz[0]), z1 = fmaf(fy, yz[3] - yz[1], yz[1]);
+    return fmaf(fz, z1 - z0, z0);
 }
 
 // Occupancy grid.  Macro-cell (X, Y, Z) covers the base records mX..mX+m-1 on
@@ -267,7 +284,7 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
         for (uint32_t b = 0; b < 32 && 32 * w + b < total; ++b) {
             const uint32_t cell = 32 * w + b;
             const uint32_t X = cell & (M - 1), Y = (cell >> lo2) & (M - 1), Z = cell >> (2 * lo2);
-            constexpr uint32_t m = 1u << kOccShift;  // base records per cell and axis
+            constexpr uint32_t m = 1u << (kOccShift > 0 ? kOccShift : 0);  // base records per cell and axis
             float bmax = -INFINITY;
             for (uint32_t dz = 0; dz < m; ++dz)
                 for (uint32_t dy = 0; dy < m; ++dy)
@@ -300,6 +317,82 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
                             dlo = fminf(dlo, l);
                             dhi = fmaxf(dhi, h);
                         }
+            }
+            const float bound = bmax + k0 - wd * (wd >= 0.0f ? dlo : dhi);
+            if (bound > -1e-5f) bits |= 1u << b;
+        }
+        occ[w] = bits;
+    }
+}
+
+// Occupancy grid of half-texel cells (kOccShift = -1): cell (X, Y, Z) covers
+// base texel-centre coordinates [X/2, X/2 + 1/2) (and likewise on y, z), inside
+// base record (X/2, Y/2, Z/2).  Trilinear interpolation restricted to a box is
+// trilinear in the box's corners, so max B over the cell is the largest of
+// B at its 8 corners (evaluated from the record); Dt over the cell's detail
+// coordinates (the same box mapped by the fixed base-to-detail shift) is
+// extreme at the box corners or at the detail lattice planes inside it, so its
+// minimum is taken over those points.  The bit is clear when
+// max B - w_d min Dt - c < -1e-5 (room for FP32 rounding).
+template <typename T>
+__global__ void occupancy_half_kernel(const T *__restrict__ base, int log2b,
+                                      const T *__restrict__ detail, int log2d, double ratio,
+                                      float dt_all_lo, float dt_all_hi, float k0, float wd,
+                                      uint32_t *__restrict__ occ) {
+    const int lc = log2b + 1;
+    const uint32_t C = 1u << lc, nd = 1u << log2d;
+    const uint32_t total = C * C * C;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < (total + 31) / 32;
+         w += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        for (uint32_t b = 0; b < 32 && 32 * w + b < total; ++b) {
+            const uint32_t cell = 32 * w + b;
+            const uint32_t K[3] = {cell & (C - 1), (cell >> lc) & (C - 1), cell >> (2 * lc)};
+            float v[8];
+            record_corners(base, ((K[2] >> 1) << (2 * log2b)) | ((K[1] >> 1) << log2b) | (K[0] >> 1), v);
+            float bmax = -INFINITY;
+            for (int r = 0; r < 8; ++r)
+                bmax = fmaxf(bmax, trilinear_at(v, 0.5f * ((K[0] & 1) + (r >> 2)),
+                                                0.5f * ((K[1] & 1) + ((r >> 1) & 1)),
+                                                0.5f * ((K[2] & 1) + (r & 1))));
+            float dlo = dt_all_lo, dhi = dt_all_hi;
+            if (detail && ratio > 0.0) {
+                // per axis: the cell's detail coordinates [lo, hi) and the points
+                // where Dt can be extreme (lo, the lattice integers inside, hi)
+                double pts[3][6];
+                int np[3];
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) {
+                    const double lo = (0.5 * K[a] + 0.5) * ratio - 0.5;
+                    const double hi = (0.5 * K[a] + 1.0) * ratio - 0.5;
+                    int n = 0;
+                    pts[a][n++] = lo;
+                    for (double q = floor(lo) + 1.0; q < hi && n < 5; q += 1.0) pts[a][n++] = q;
+                    if (floor(lo) + 1.0 + (n - 1) < hi) ok = false;  // more planes than kept
+                    pts[a][n++] = hi;
+                    np[a] = n;
+                }
+                if (ok) {
+                    dlo = INFINITY;
+                    dhi = -INFINITY;
+                    for (int iz = 0; iz < np[2]; ++iz)
+                        for (int iy = 0; iy < np[1]; ++iy)
+                            for (int ix = 0; ix < np[0]; ++ix) {
+                                const double sp[3] = {pts[0][ix], pts[1][iy], pts[2][iz]};
+                                uint32_t ri[3];
+                                float f[3];
+                                for (int a = 0; a < 3; ++a) {
+                                    const double fl = floor(sp[a]);
+                                    ri[a] = (uint32_t)((long long)fl & (long long)(nd - 1));
+                                    f[a] = (float)(sp[a] - fl);
+                                }
+                                float dv[8];
+                                record_corners(detail, (ri[2] << (2 * log2d)) | (ri[1] << log2d) | ri[0], dv);
+                                const float val = trilinear_at(dv, f[0], f[1], f[2]);
+                                dlo = fminf(dlo, val);
+                                dhi = fmaxf(dhi, val);
+                            }
+                }
             }
             const float bound = bmax + k0 - wd * (wd >= 0.0f ? dlo : dhi);
             if (bound > -1e-5f) bits |= 1u << b;
@@ -384,9 +477,14 @@ int build_occupancy(cloud_volume *v, cudaStream_t s) {
         cudaFree(d_range);
         if (rc) return rc;
     }
-    occupancy_kernel<T><<<grid_for(words, 128), 128, 0, s>>>(
-        (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, ratio, range[0],
-        range[1], k0, (float)wd, v->occ);
+    if (kOccShift < 0)
+        occupancy_half_kernel<T><<<grid_for(words, 128), 128, 0, s>>>(
+            (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, ratio, range[0],
+            range[1], k0, (float)wd, v->occ);
+    else
+        occupancy_kernel<T><<<grid_for(words, 128), 128, 0, s>>>(
+            (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, ratio, range[0],
+            range[1], k0, (float)wd, v->occ);
     return check_launch("occupancy_kernel");
 }
 

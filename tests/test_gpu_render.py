@@ -171,40 +171,57 @@ def test_occupancy_skip_is_bitwise_exact(api, frame, precision):
     assert int(n_full.item()) == int(n_skip.item())  # the same lookups, fewer of them read memory
 
 
+def _half_lattice(t):
+    """Trilinear values of a periodic texel lattice at every half-texel point:
+    index 2k is texel k, 2k + 1 the midpoint of texels k and k + 1 (per axis)."""
+    h = np.zeros((2 * t.shape[0],) * 3)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                acc, cnt = 0.0, 0
+                for oz in range(dz + 1):
+                    for oy in range(dy + 1):
+                        for ox in range(dx + 1):
+                            acc = acc + np.roll(t, (-oz, -oy, -ox), (0, 1, 2))
+                            cnt += 1
+                h[dz::2, dy::2, dx::2] = acc / cnt
+    return h
+
+
 def test_occupancy_grid_is_conservative(api, oracle):
-    """Every macro-cell the grid marks empty really has no density: checked on
-    the FP64 oracle texels (max B - w_d min Dt - c < 0 over the base and detail
-    texels any sample of the cell interpolates), and the grid marks a
-    substantial share of the cells empty."""
+    """Every cell the grid marks empty really has no density, checked on the FP64
+    oracle texels, and the grid marks a substantial share of the cells empty.
+    A grid cell is half a base texel on each axis: over it, trilinear B is
+    largest at one of the cell's 8 corners (half-texel lattice points), and Dt
+    over the same box (detail coordinate = 2 x base + 1/2 here) is smallest at
+    one of the 27 points formed by its corners and the detail lattice plane
+    inside; max B - w_d min Dt - c must then be negative."""
     desc = I.volume_desc("full", seed=3)
     occ = api.Volume(desc).occupancy()
     ov = oracle.Volume(desc)
     B, Dt = ov.base, ov.detail
     nb, nd = B.shape[0], Dt.shape[0]
-    m = nb // occ.shape[0]  # base records per cell and axis
-    assert occ.shape == (nb // m,) * 3 and m in (1, 2)
-    Bp = np.pad(B, ((0, m), (0, m), (0, m)), mode="wrap")
+    assert occ.shape == (2 * nb,) * 3
+    assert desc["base_period"] / desc["detail_period"] * nd / nb == 2.0
+    bh = np.pad(_half_lattice(B), ((0, 1),) * 3, mode="wrap")
     bmax = np.full(occ.shape, -np.inf)
-    for dz in range(m + 1):
-        for dy in range(m + 1):
-            for dx in range(m + 1):
-                bmax = np.maximum(bmax, Bp[dz:dz + nb:m, dy:dy + nb:m, dx:dx + nb:m])
-    # detail texels of base cell K (base texels mK..mK+m at 2 detail texels each,
-    # base period = 8 detail periods): detail texels 2mK .. 2mK+2m+1 (mod nd)
-    ratio = desc["base_period"] / desc["detail_period"] * nd / nb
-    assert ratio == 2.0
-    w = 2 * m + 2
-    Dp = np.pad(Dt, ((0, w), (0, w), (0, w)), mode="wrap")
-    dmin = np.full((nd // (2 * m),) * 3, np.inf)
-    for dz in range(w):
-        for dy in range(w):
-            for dx in range(w):
-                dmin = np.minimum(dmin, Dp[dz:dz + nd:2 * m, dy:dy + nd:2 * m, dx:dx + nd:2 * m])
-    k = np.arange(nb // m) % (nd // (2 * m))
-    dmin_cells = dmin[np.ix_(k, k, k)]
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                bmax = np.maximum(bmax, bh[dz:dz + 2 * nb, dy:dy + 2 * nb, dx:dx + 2 * nb])
+    # cell u: detail coordinates [u + 1/2, u + 3/2) -> half-lattice points 2u+1, 2u+2, 2u+3
+    dh = _half_lattice(Dt)
+    dhp = np.pad(dh, ((0, 3),) * 3, mode="wrap")
+    dmin = np.full(dh.shape, np.inf)
+    for oz in (1, 2, 3):
+        for oy in (1, 2, 3):
+            for ox in (1, 2, 3):
+                dmin = np.minimum(dmin, dhp[oz:oz + 2 * nd, oy:oy + 2 * nd, ox:ox + 2 * nd])
+    k = np.arange(2 * nb) % nd
+    dmin_cells = dmin[::2, ::2, ::2][np.ix_(k, k, k)]
     bound = bmax - desc["detail_weight"] * dmin_cells - desc["coverage"]
     empty = ~occ
-    assert empty.mean() > 0.2
+    assert empty.mean() > 0.5
     assert bound[empty].max() < 0.0
 
 
