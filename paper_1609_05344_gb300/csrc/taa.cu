@@ -252,11 +252,28 @@ __global__ void __launch_bounds__(256) taa_kernel(const H *__restrict__ hist,
 // computed in registers (the motion kernel's arithmetic, bitwise) instead
 // of being written and read back; the current frame's 3x3 neighbourhoods come
 // from a shared-memory tile with a clamped one-pixel halo, brought in by one
-// TMA bulk tensor copy while the motion is computed; each thread resolves two
-// vertically adjacent pixels, whose 3x3 windows share two rows.
-constexpr int kTW = 32, kTH = 16;  // pixel tile of a 32x8-thread CTA
+// TMA bulk tensor copy while the motion is computed; each thread resolves
+// ResolvePix<H> vertically adjacent pixels, whose 3x3 windows share rows, and
+// filters their history footprints before it waits for the tile.
+#ifndef CLOUDVOL_TAA_PIX_F32
+#define CLOUDVOL_TAA_PIX_F32 4  // pixels per thread, FP32 history (79 registers)
+#endif
+#ifndef CLOUDVOL_TAA_PIX_F16
+#define CLOUDVOL_TAA_PIX_F16 2  // pixels per thread, FP16 history
+#endif
+template <typename H>
+struct ResolvePix {
+    static constexpr int value = CLOUDVOL_TAA_PIX_F32;
+    static constexpr int rows = 8 * value;  // pixel rows of a tile
+};
+template <>
+struct ResolvePix<uint2> {
+    static constexpr int value = CLOUDVOL_TAA_PIX_F16;
+    static constexpr int rows = 8 * value;
+};
+constexpr int kTW = 32;  // pixel tile of a 32x8-thread CTA: 32 x ResolvePix<H>::rows
 #ifndef CLOUDVOL_TAA_MIN_BLOCKS
-#define CLOUDVOL_TAA_MIN_BLOCKS 3  // CTAs per SM the fused kernel is compiled for (74 registers)
+#define CLOUDVOL_TAA_MIN_BLOCKS 3  // CTAs per SM the fused kernel is compiled for
 #endif
 
 // Waits that gave up (a bulk copy that did not complete in time): counted on
@@ -302,8 +319,9 @@ template <typename H>
 __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const MotionParams &mp,
                                              const H *__restrict__ hist, H *__restrict__ out,
                                              float blend, int bx, int by,
-                                             float4 (&tile)[kTH + 2][kTW + 2], uint64_t &bar,
-                                             int first_polls, unsigned int *status) {
+                                             float4 (&tile)[ResolvePix<H>::rows + 2][kTW + 2],
+                                             uint64_t &bar, int first_polls, unsigned int *status) {
+    constexpr int kPix = ResolvePix<H>::value, kTH = ResolvePix<H>::rows;
     const int W = mp.width, Hh = mp.height;
     const int x0 = bx * kTW, y0 = by * kTH;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -330,27 +348,29 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
               "r"(smem_addr(&bar))
             : "memory");
     }
-    // 2. motion (registers only) and the history footprint of both pixels
-    //    (rows 2 ty and 2 ty + 1 of the tile): column terms once, the two
-    //    pixels' arithmetic interleaved, the rare near-tie calls after
-    bool use[2] = {false, false};
-    float fxs[2] = {0.f, 0.f}, fys[2] = {0.f, 0.f};
-    float4 h00[2], h01[2], h10[2], h11[2];
+    // 2. motion (registers only) and the history footprint of the thread's
+    //    pixels (rows kPix ty .. kPix ty + kPix - 1 of the tile): column terms
+    //    once, the pixels' arithmetic interleaved, the rare near-tie calls after
+    bool use[kPix];
+    float fxs[kPix], fys[kPix];
+    float4 h00[kPix], h01[kPix], h10[kPix], h11[kPix];
+#pragma unroll
+    for (int r = 0; r < kPix; ++r) use[r] = false;
     if (hist && x < W) {
         const MotionCol col = motion_col(mp, x);
-        float bs[2], lam[2];
-        bool ex[2];
+        float bs[kPix], lam[kPix];
+        bool ex[kPix];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            bs[r] = fmaf((float)(y0 + 2 * ty + r), mp.by, mp.b0);
+        for (int r = 0; r < kPix; ++r) {
+            bs[r] = fmaf((float)(y0 + kPix * ty + r), mp.by, mp.b0);
             lam[r] = motion_lambda(mp, col, bs[r], &ex[r]);
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
-            if (ex[r]) lam[r] = entry_lambda_exact(mp, x, y0 + 2 * ty + r);
+        for (int r = 0; r < kPix; ++r)
+            if (ex[r]) lam[r] = entry_lambda_exact(mp, x, y0 + kPix * ty + r);
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int y = y0 + 2 * ty + r;
+        for (int r = 0; r < kPix; ++r) {
+            const int y = y0 + kPix * ty + r;
             if (y >= Hh) continue;
             const float2 m = motion_project(mp, col, bs[r], lam[r]);
             const float xc = (float)x + 0.5f, yc = (float)y + 0.5f;
@@ -363,13 +383,18 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
             const int xa = min(max(ix, 0), W - 1), xb = min(max(ix + 1, 0), W - 1);
             const int ya = min(max(iy, 0), Hh - 1), yb = min(max(iy + 1, 0), Hh - 1);
             if (!in_range(mp.check, xa >= 0 && xb < W && ya >= 0 && yb < Hh, kChkHistory)) continue;
-            h00[r] = load_hist(hist, (size_t)ya * W + xa);
-            h01[r] = load_hist(hist, (size_t)ya * W + xb);
-            h10[r] = load_hist(hist, (size_t)yb * W + xa);
-            h11[r] = load_hist(hist, (size_t)yb * W + xb);
+            const H *ra = hist + (size_t)ya * W, *rb = hist + (size_t)yb * W;
+            h00[r] = load_hist(ra, xa);
+            h01[r] = load_hist(ra, xb);
+            h10[r] = load_hist(rb, xa);
+            h11[r] = load_hist(rb, xb);
             use[r] = true;
         }
     }
+    float4 hf[kPix];  // filtered history, before the wait for the tile
+#pragma unroll
+    for (int r = 0; r < kPix; ++r)
+        if (use[r]) hf[r] = bil4(fxs[r], fys[r], h00[r], h01[r], h10[r], h11[r]);
     __syncthreads();  // the barrier's initialisation is visible to every thread
     const bool landed = mbar_wait(&bar, 0, first_polls);
     if (!__syncthreads_and(landed)) {
@@ -402,30 +427,29 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
         __syncthreads();
     }
     if (x >= W) return;
-    if (!in_range(mp.check, tx + 2 < kTW + 2 && 2 * ty + 3 < kTH + 2, kChkTile)) return;
-    // 3. 3x3 ranges of both pixels from four tile rows (three-input min/max):
-    //    the two rows both windows share are reduced once, each pixel adds
-    //    its own third row; clamp the filtered history, blend
-    float4 mn12, mx12;  // rows 2 ty + 1 and 2 ty + 2, shared by both pixels
-    {
-        const float4 a1 = tile[2 * ty + 1][tx], b1 = tile[2 * ty + 1][tx + 1], c1 = tile[2 * ty + 1][tx + 2];
-        const float4 a2 = tile[2 * ty + 2][tx], b2 = tile[2 * ty + 2][tx + 1], c2 = tile[2 * ty + 2][tx + 2];
-        mn12 = fmin4(min3_4(a1, b1, c1), min3_4(a2, b2, c2));
-        mx12 = fmax4(max3_4(a1, b1, c1), max3_4(a2, b2, c2));
-    }
+    if (!in_range(mp.check, tx + 2 < kTW + 2 && kPix * ty + kPix + 1 < kTH + 2, kChkTile)) return;
+    // 3. 3x3 ranges from the kPix + 2 tile rows the thread's windows cover
+    //    (three-input min/max): each row's three texels reduced once, each
+    //    pixel combines three row results as soon as its last row is in;
+    //    clamp the filtered history, blend
+    float4 rmn[kPix + 2], rmx[kPix + 2], cen[kPix + 2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int y = y0 + 2 * ty + r;
+    for (int j = 0; j < kPix + 2; ++j) {
+        const float4 a = tile[kPix * ty + j][tx], b = tile[kPix * ty + j][tx + 1],
+                     d = tile[kPix * ty + j][tx + 2];
+        rmn[j] = min3_4(a, b, d);
+        rmx[j] = max3_4(a, b, d);
+        cen[j] = b;
+        if (j < 2) continue;
+        const int r = j - 2;  // the pixel whose window ends at row j
+        const int y = y0 + kPix * ty + r;
         if (y >= Hh) continue;
-        const float4 c = tile[2 * ty + r + 1][tx + 1];
+        const float4 c = cen[r + 1];
         float4 res = c;
         if (use[r]) {
-            const int k = 2 * ty + 3 * r;  // the row of the pair's window not shared
-            const float4 a = tile[k][tx], b = tile[k][tx + 1], d = tile[k][tx + 2];
-            const float4 mn = min3_4(mn12, a, min3_4(b, d, b));
-            const float4 mx = max3_4(mx12, a, max3_4(b, d, b));
-            const float4 h = bil4(fxs[r], fys[r], h00[r], h01[r], h10[r], h11[r]);
-            res = blend4(fmin4(fmax4(h, mn), mx), c, blend);
+            const float4 mn = min3_4(rmn[r], rmn[r + 1], rmn[r + 2]);
+            const float4 mx = max3_4(rmx[r], rmx[r + 1], rmx[r + 2]);
+            res = blend4(fmin4(fmax4(hf[r], mn), mx), c, blend);
         }
         if (in_range(mp.check, y >= 0 && x >= 0, kChkPixel)) store_hist(out, (size_t)y * W + x, res);
     }
@@ -436,7 +460,7 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
     taa_reproject_kernel(const __grid_constant__ CUtensorMap tile_map,
                          const __grid_constant__ MotionParams mp, const H *__restrict__ hist,
                          H *__restrict__ out, float blend, int first_polls, unsigned int *status) {
-    __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(128) float4 tile[ResolvePix<H>::rows + 2][kTW + 2];
     __shared__ __align__(8) uint64_t bar;
     resolve_tile<H>(&tile_map, mp, hist, out, blend, blockIdx.x, blockIdx.y, tile, bar, first_polls,
                     status);
@@ -459,7 +483,7 @@ template <typename H>
 __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
     taa_reproject_batch_kernel(const ResolveView *__restrict__ views, int n_views, int first_polls,
                                unsigned int *status) {
-    __shared__ __align__(128) float4 tile[kTH + 2][kTW + 2];
+    __shared__ __align__(128) float4 tile[ResolvePix<H>::rows + 2][kTW + 2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ MotionParams smp;
     __shared__ int s_view;
@@ -586,9 +610,9 @@ int launch_taa(const void *history, const float *current, const float *motion, v
 
 // Tensor map of the current frame for the resolve's tile copy: the frame as
 // a 2-D FP32 array of 4 W x H elements (row stride 16 W bytes), box 4 (kTW + 2)
-// x (kTH + 2) elements, zero fill outside.  The encoder is the driver's,
+// x (rows + 2) elements, zero fill outside.  The encoder is the driver's,
 // fetched through the runtime once.
-static int current_tile_map(const float *current, int width, int height, CUtensorMap *map) {
+static int current_tile_map(const float *current, int width, int height, int rows, CUtensorMap *map) {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     std::call_once(once, [] {
@@ -602,7 +626,7 @@ static int current_tile_map(const float *current, int width, int height, CUtenso
     if (!encode) return set_error(CLOUD_ERR_CUDA, "cloud_taa_reproject: cuTensorMapEncodeTiled unavailable");
     const cuuint64_t dims[2] = {4ull * (cuuint64_t)width, (cuuint64_t)height};
     const cuuint64_t strides[1] = {16ull * (cuuint64_t)width};
-    const cuuint32_t box[2] = {4u * (kTW + 2), (cuuint32_t)(kTH + 2)};
+    const cuuint32_t box[2] = {4u * (kTW + 2), (cuuint32_t)(rows + 2)};
     const cuuint32_t elem[2] = {1u, 1u};
     const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(current), dims,
                               strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -631,9 +655,10 @@ int launch_taa_reproject(const cloud_volume *vol, const cloud_params *prm, const
         if (a < b + px * eb && b < a + px * eb)
             return set_error(CLOUD_ERR_INVALID_ARG, "cloud_taa_reproject: history and history_out overlap");
     }
+    const int rows = fmt == CLOUD_HISTORY_FP32 ? ResolvePix<float4>::rows : ResolvePix<uint2>::rows;
     CUtensorMap map;
-    if (int rc = current_tile_map(current, width, height, &map)) return rc;
-    const dim3 grid((width + kTW - 1) / kTW, (height + kTH - 1) / kTH), block(32, 8);
+    if (int rc = current_tile_map(current, width, height, rows, &map)) return rc;
+    const dim3 grid((width + kTW - 1) / kTW, (height + rows - 1) / rows), block(32, 8);
     const int polls = g_first_polls.load();
     if (fmt == CLOUD_HISTORY_FP32)
         taa_reproject_kernel<float4><<<grid, block, 0, s>>>(map, p, (const float4 *)history,
@@ -659,6 +684,7 @@ int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
     ResolveView *h_table = static_cast<ResolveView *>(h_table_v);
     int next = 0;
     const size_t eb = fmt == CLOUD_HISTORY_FP32 ? 16 : 8;
+    const int rows = fmt == CLOUD_HISTORY_FP32 ? ResolvePix<float4>::rows : ResolvePix<uint2>::rows;
     for (int i = 0; i < n; ++i) {
         const ResolveRequest &r = reqs[i];
         if (!r.cur || !r.current || !r.out || (r.history && !r.prev))
@@ -675,13 +701,13 @@ int launch_taa_reproject_batch(const cloud_volume *vol, const cloud_params *prm,
             if (a < b + px * eb && b < a + px * eb)
                 return set_error(CLOUD_ERR_INVALID_ARG, "resolve batch: history and output overlap");
         }
-        if (int rc = current_tile_map(r.current, r.width, r.height, &v.map)) return rc;
+        if (int rc = current_tile_map(r.current, r.width, r.height, rows, &v.map)) return rc;
         v.hist = r.history;
         v.out = r.out;
         v.blend = blend;
         v.tiles_x = (r.width + kTW - 1) / kTW;
         v.tile_begin = next;
-        next += v.tiles_x * ((r.height + kTH - 1) / kTH);
+        next += v.tiles_x * ((r.height + rows - 1) / rows);
     }
     if (int rc = check_cuda(cudaMemcpyAsync(d_table_v, h_table, sizeof(ResolveView) * n,
                                             cudaMemcpyHostToDevice, s),

@@ -337,7 +337,7 @@ def test_resolve_wait_give_up_is_reported(api):
     from paper_1609_05344_gb300 import _native as N
     vol = api.Volume(I.volume_desc("tiny", seed=1))
     prm = I.params()
-    w, h, tiles = 70, 37, 3 * 3  # 32x16-pixel tiles: 3 columns, 3 rows (ragged)
+    w, h, tiles = 70, 37, 3 * 2  # FP32 history: 32x32-pixel tiles, 3 columns, 2 rows (ragged)
     cams = [I.orbit_camera(f, 1) for f in range(3)]
     torch.cuda.synchronize()
     before = api.device_wait_timeouts()
