@@ -327,7 +327,7 @@ __device__ __forceinline__ void resolve_tile(const CUtensorMap *tile_map, const 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = x0 + tx;
     const int tid = ty * 32 + tx;
-    // 1. current-frame tile with a one-pixel halo (34 x 18 texels), one TMA
+    // 1. current-frame tile with a one-pixel halo (34 x kTH + 2 texels), one TMA
     //    bulk copy issued by one thread, landing while the motion is computed.
     //    The box starts at texel (x0 - 1, y0 - 1): its x offset in bytes is
     //    16 (x0 - 1), a multiple of 16; texels outside the frame arrive as
