@@ -156,9 +156,11 @@ __device__ __forceinline__ df df_mulf(df a, float b) {
     const float e = fmaf(a.hi, b, -p);
     return fast_two_sum(p, fmaf(a.lo, b, e));
 }
-// 1/b: one Newton step on the FP32 reciprocal.
+// 1/b: one Newton step on the hardware reciprocal estimate (PTX rcp.approx,
+// relative error about 2^-23; the step squares it, like df_rsqrt's).
 __device__ __forceinline__ df df_recip(df b) {
-    const float q = __frcp_rn(b.hi);
+    float q;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(q) : "f"(b.hi));
     const df p = df_mulf(b, q);                 // b q = 1 - r
     const float r = (1.0f - p.hi) - p.lo;
     return fast_two_sum(q, q * r);

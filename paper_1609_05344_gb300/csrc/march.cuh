@@ -328,17 +328,25 @@ __device__ __forceinline__ unsigned long long march_tile(
             a = df_addf(a, xf * v.vxh[k]);  // exact products
             r[k] = df_addf(a, yf * v.vyh[k]);
         }
-        const df n2 = df_add(df_add(df_mul(r[0], r[0]), df_mul(r[1], r[1])), df_mul(r[2], r[2]));
-        const df rn = df_rsqrt(n2);  // 1 / |v|
-        const df lam_max = df_mul({v.tmax_h, v.tmax_l}, rn);
-        df lam0 = {0.0f, 0.0f}, lam1 = lam_max;
-        if (fabsf(r[2].hi) * rn.hi < 1e-8f) {
+        // |v| in FP32 for the step length and the phase angle; the far clip
+        // lambda_max = t_max / |v| in double-float only where it can decide the
+        // layer exit (an FP32 test with a 1e-5 margin, far above its error)
+        const float n2f = fmaf(r[0].hi, r[0].hi, fmaf(r[1].hi, r[1].hi, r[2].hi * r[2].hi));
+        const float rnf = rsqrtf(n2f);  // 1 / |v|
+        const auto lam_max = [&]() {
+            const df n2 = df_add(df_add(df_mul(r[0], r[0]), df_mul(r[1], r[1])), df_mul(r[2], r[2]));
+            return df_mul({v.tmax_h, v.tmax_l}, df_rsqrt(n2));
+        };
+        df lam0 = {0.0f, 0.0f}, lam1;
+        if (fabsf(r[2].hi) * rnf < 1e-8f) {
             alive = v.cam_in_layer != 0;
+            lam1 = lam_max();
         } else {
             const df inv = df_recip(r[2]);
             const df ll = df_mul({v.zlo_h, v.zlo_l}, inv), lh = df_mul({v.zhi_h, v.zhi_l}, inv);
             lam0 = df_max(df_min(ll, lh), lam0);
-            lam1 = df_min(df_max(ll, lh), lam_max);
+            lam1 = df_max(ll, lh);
+            if (!(lam1.hi < v.tmax_h * rnf * (1.0f - 1e-5f))) lam1 = df_min(lam1, lam_max());
             alive = df_gt(lam1, lam0);
         }
         if (alive) {
@@ -375,11 +383,11 @@ __device__ __forceinline__ unsigned long long march_tile(
             const df hrel = df_add(df_mul(lam_s, r[2]), df_neg({v.zlo_h, v.zlo_l}));
             hq = (int32_t)df_to_u32({hrel.hi * 65536.0f, hrel.lo * 65536.0f});
             eh = (int32_t)df_to_u32({dpos[2].hi * 65536.0f, dpos[2].lo * 65536.0f});
-            const float vlen = n2.hi * rn.hi;
+            const float vlen = n2f * rnf;
             Df = D.hi * vlen;
             // --- a5: phase function, hoisted per ray ----------------------------
             // p_HG(mu) = (1 - g^2) / (4 pi) * (1 + g^2 - 2 g mu)^(-3/2)
-            const float mu = (r[0].hi * p.sun[0] + r[1].hi * p.sun[1] + r[2].hi * p.sun[2]) * rn.hi;
+            const float mu = (r[0].hi * p.sun[0] + r[1].hi * p.sun[1] + r[2].hi * p.sun[2]) * rnf;
             const float q = rsqrtf(fmaf(-2.0f * p.hg_g, mu, fmaf(p.hg_g, p.hg_g, 1.0f)));
             phase = p.hg_norm * q * q * q;
         }
