@@ -15,7 +15,9 @@ and the integration rules of Sec. 3.1.
 * Convergence: analytic and basic rules approach the same limit as N grows.
 * By hand: one and two (jittered) view steps of a pixel written out from the
   method's formulas, sharing only the separately pinned density and hash with
-  the oracle, pin the light-march placement and sum and the step chaining.
+  the oracle, pin the light-march placement and sum and the step chaining;
+  every pixel of small images recomputed the same way pins the assembled
+  image, the early out and the lookup count.
 """
 import math
 
@@ -330,3 +332,71 @@ def test_two_jittered_steps_by_hand(oracle):
         assert np.allclose(got[y, x], want, rtol=1e-12, atol=1e-14), yaw
         checked += tau > 0
     assert checked >= 5
+
+
+def _pixel_by_hand(oracle, vol, desc, prm, cam, w, h, x, y, n, ls, frame, basic):
+    """One pixel of Sec. 1 / Sec. 3.1 / Sec. 3.2 written out: view samples at
+    t0 + (i + u) D, a light march of ls samples towards the sun where the view
+    density is positive, L_in = E e^{-tau_sun} p_HG + A, the analytic (or basic)
+    step, and the early out once tau reaches tau_max.  Returns RGBA and the
+    number of density lookups (view samples walked plus light samples)."""
+    s = np.array(prm["sun_dir"]) / np.linalg.norm(prm["sun_dir"])
+    al, dl = prm["absorption"], prm["light_step"]
+    d = oracle.pixel_ray(cam, w, h, x, y)
+    o = np.array(cam["pos"])
+    hit, t0, t1 = oracle.slab_clip(desc, prm, o, d)
+    if not hit:
+        return np.zeros(4), 0
+    u = oracle.jitter(desc["seed"], x, y, frame) if frame >= 0 else 0.5
+    D = (t1 - t0) / n
+    ph = oracle.hg(float(np.dot(d, s)), prm["hg_g"])
+    c, tau, looks = np.zeros(3), 0.0, 0
+    for i in range(n):
+        p = o + (t0 + (i + u) * D) * d
+        rho = vol.density(p)
+        looks += 1
+        if rho > 0.0:
+            tsun = al * dl * sum(vol.density(p + (j + 0.5) * dl * s) for j in range(ls))
+            looks += ls
+            lin = np.array(prm["sun_radiance"]) * math.exp(-tsun) * ph + np.array(prm["ambient"])
+            sd = al * rho * D
+            if basic:
+                c += math.exp(-(tau + sd)) * sd * lin
+            else:
+                c += math.exp(-tau) * lin * -math.expm1(-sd)
+            tau += sd
+        if tau >= prm["tau_max"]:
+            break
+    return np.concatenate([c, [-math.expm1(-tau)]]), looks
+
+
+@pytest.mark.parametrize("pos,yaw,pitch", [((0.0, 0.0, 500.0), 30.0, 14.0),
+                                           ((300.0, -200.0, 2600.0), 200.0, -4.0),
+                                           ((0.0, 0.0, 6000.0), 120.0, -28.0)])
+@pytest.mark.parametrize("tau_max,basic", [(11.5, False), (0.7, False), (11.5, True)])
+def test_small_images_by_hand(oracle, pos, yaw, pitch, tau_max, basic):
+    """Every pixel of small jittered images, camera below, inside and above the
+    layer, recomputed from the method's formulas with only the separately
+    pinned pieces (pixel ray, layer clip, jitter hash, density, HG) shared with
+    the oracle: pins the assembled image -- sample placement, light marches,
+    step chaining, both integration rules, the early out (tau_max = 0.7 trips
+    it) and the lookup count -- to 1e-12."""
+    desc = I.volume_desc("full", seed=11)
+    vol = oracle.Volume(desc)
+    prm = I.params(tau_max=tau_max)
+    cam = I.camera(pos, yaw, pitch, 70.0)
+    w, h, n, ls, frame = 7, 5, 8, 6, 3
+    integ = oracle.BASIC if basic else oracle.ANALYTIC
+    got, n_got = oracle.render(vol, cam, prm, w, h, n, ls, jitter_frame=frame, integration=integ)
+    n_want, lit, early = 0, 0, 0
+    for y in range(h):
+        for x in range(w):
+            want, looks = _pixel_by_hand(oracle, vol, desc, prm, cam, w, h, x, y, n, ls, frame, basic)
+            n_want += looks
+            lit += want[3] > 0
+            early += looks < n * (1 + ls) and want[3] >= -math.expm1(-tau_max)
+            assert np.allclose(got[y, x], want, rtol=1e-12, atol=1e-14), (x, y)
+    assert n_got == n_want
+    assert lit >= 10  # most pixels see cloud
+    if tau_max < 1.0:
+        assert early >= 2  # the early out ended rays
