@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
 // is found by binary search over the views' first tile indices and staged in
 // shared memory.
 template <typename T, int LS, int SHAPE, bool FX, int CH>
-__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
+__global__ void __launch_bounds__(128, BatchBlocks<T, FX>::value)
     march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
                        int n_views, int total_tiles, unsigned int *__restrict__ work,
                        const T *__restrict__ base, const T *__restrict__ detail,
