@@ -40,15 +40,6 @@ template <>
 struct MarchBlocks<float, false> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32; };
 template <>
 struct MarchBlocks<float, true> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX; };
-// The persistent multi-view kernel carries its work-queue state as well: 7 CTAs
-// for FP32 records at the standard sizes (8-16 bytes of spills; 8 CTAs: 20).
-#ifndef CLOUDVOL_MARCH_BATCH_MIN_BLOCKS_F32_FX
-#define CLOUDVOL_MARCH_BATCH_MIN_BLOCKS_F32_FX 7
-#endif
-template <typename T, bool FX>
-struct BatchBlocks { static constexpr int value = MarchBlocks<T, FX>::value; };
-template <>
-struct BatchBlocks<float, true> { static constexpr int value = CLOUDVOL_MARCH_BATCH_MIN_BLOCKS_F32_FX; };
 
 // The standard tile sizes (128^3 base, 32^3 detail, 512^2 weather records) as
 // compile-time constants: with FX the record-index and weight shifts of every
@@ -164,13 +155,22 @@ inline int config_shape(int config) { return config % kShapes; }
 inline int config_chunk(int config) { return CHSizes[(config / kShapes) & 1]; }
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Axes whose start and increment a warp stages for step_coords: all of them,
+// or (FX: the base tile period is 2^detail_shift detail periods) the base,
+// weather and height axes only, the detail coordinates following from the
+// base ones by an exact shift.
+template <bool FX>
+struct StagedAxes { static constexpr int value = kAxes; };
+template <>
+struct StagedAxes<true> { static constexpr int value = 6; };  // BX BY BZ WX WY, height
+
 // Per-warp shared scratch of the march: each lane's start coordinates and
 // per-step increments, the chunk's view densities, light-march sums and the
 // list of (step, lane) pairs that need a light march (CH view steps a chunk).
-template <int CH>
+template <int CH, bool FX>
 struct WarpScratch {
-    uint32_t c0[kAxes][32];
-    uint32_t e[kAxes][32];
+    uint32_t c0[StagedAxes<FX>::value][32];
+    uint32_t e[StagedAxes<FX>::value][32];
     float rho[CH][32];
     float lsum[CH][32];
     uint16_t pairs[CH * 32];
@@ -272,15 +272,43 @@ __device__ __forceinline__ float density(const SceneParams &p, const T *__restri
     return g * w * r;
 }
 
+// Staging of one lane's start coordinates and increments (lattice axes, then
+// the height) into the warp's scratch.
+template <int CH, bool FX>
+__device__ __forceinline__ void stage_coords(WarpScratch<CH, FX> &ws, unsigned lane,
+                                             const uint32_t c[kLatticeAxes],
+                                             const uint32_t e[kLatticeAxes], int32_t hq, int32_t eh) {
+    constexpr int kS = StagedAxes<FX>::value;
+#pragma unroll
+    for (int a = 0, s = 0; a < kLatticeAxes; ++a) {
+        if (FX && a >= kDX && a <= kDZ) continue;
+        ws.c0[s][lane] = c[a];
+        ws.e[s][lane] = e[a];
+        ++s;
+    }
+    ws.c0[kS - 1][lane] = (uint32_t)hq;
+    ws.e[kS - 1][lane] = (uint32_t)eh;
+}
+
 // Coordinates of view step i of ray `ow` of the warp from its staged start and
 // increment (integer arithmetic: the same values as adding the increment step
-// by step).
-__device__ __forceinline__ int32_t step_coords(const uint32_t (&c0)[kAxes][32],
-                                               const uint32_t (&e)[kAxes][32], unsigned ow,
-                                               uint32_t i, uint32_t cs[kLatticeAxes]) {
+// by step; for FX the detail coordinates are the base ones shifted exactly,
+// as the ray setup derives them).  Returns the height.
+template <int CH, bool FX>
+__device__ __forceinline__ int32_t step_coords(const SceneParams &p, const WarpScratch<CH, FX> &ws,
+                                               unsigned ow, uint32_t i, uint32_t cs[kLatticeAxes]) {
+    constexpr int kS = StagedAxes<FX>::value;
 #pragma unroll
-    for (int a = 0; a < kLatticeAxes; ++a) cs[a] = c0[a][ow] + i * e[a][ow];
-    return (int32_t)(c0[kLatticeAxes][ow] + i * e[kLatticeAxes][ow]);
+    for (int a = 0, s = 0; a < kLatticeAxes; ++a) {
+        if (FX && a >= kDX && a <= kDZ) {
+            const int b = a - kDX;
+            cs[a] = ((cs[b] + p.half_unit[b]) << p.detail_shift) - p.half_unit[a];
+            continue;
+        }
+        cs[a] = ws.c0[s][ow] + i * ws.e[s][ow];
+        ++s;
+    }
+    return (int32_t)(ws.c0[kS - 1][ow] + i * ws.e[kS - 1][ow]);
 }
 
 // sigma D of one step, rounded the same way wherever it is recomputed
@@ -305,7 +333,7 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 // view step walked, plus the light steps of each step with density).
 template <typename T, int LS, int SHAPE, bool FX, int CH>
 __device__ __forceinline__ unsigned long long march_tile(
-    const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch<CH> &ws,
+    const SceneParams &p, const ViewParams &v, int tile_x, int tile_y, WarpScratch<CH, FX> &ws,
     const T *__restrict__ base, const T *__restrict__ detail, const T *__restrict__ weather) {
     using S = TileShape<SHAPE>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -403,13 +431,7 @@ __device__ __forceinline__ unsigned long long march_tile(
             phase = p.hg_norm * q * q * q;
         }
     }
-#pragma unroll
-    for (int a = 0; a < kLatticeAxes; ++a) {
-        ws.c0[a][lane] = c[a];
-        ws.e[a][lane] = e[a];
-    }
-    ws.c0[kLatticeAxes][lane] = (uint32_t)hq;
-    ws.e[kLatticeAxes][lane] = (uint32_t)eh;
+    stage_coords(ws, lane, c, e, hq, eh);
     const unsigned lt_mask = (1u << lane) - 1u;
     float tau = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     for (int i0 = 0; i0 < v.steps && __any_sync(kFull, alive); i0 += CH) {
@@ -461,7 +483,7 @@ __device__ __forceinline__ unsigned long long march_tile(
 #pragma unroll
             for (int b = 0; b < kViewBatch; ++b) {
                 uint32_t cs[kLatticeAxes];
-                const int32_t hs = step_coords(ws.c0, ws.e, pr[b] & 31u, (uint32_t)i0 + (pr[b] >> 5), cs);
+                const int32_t hs = step_coords(p, ws, pr[b] & 31u, (uint32_t)i0 + (pr[b] >> 5), cs);
                 rho[b] = density<FX>(p, base, detail, weather, cs, hs);
             }
 #pragma unroll
@@ -511,7 +533,7 @@ __device__ __forceinline__ unsigned long long march_tile(
             const unsigned pr = ws.pairs[q], k = pr >> 5, ow = pr & 31u;
             if (!in_range(p.check, q < CH * 32u && k < (unsigned)CH, kChkWork)) continue;
             uint32_t cs[kLatticeAxes];
-            const int32_t hs = step_coords(ws.c0, ws.e, ow, (uint32_t)(i0 + (int)k), cs);
+            const int32_t hs = step_coords(p, ws, ow, (uint32_t)(i0 + (int)k), cs);
             float rho_sum = 0.0f;
             if (LS >= 0) {
                 constexpr int kU = LightUnroll<T>::value;
@@ -591,7 +613,8 @@ void launch_march_ch(const SceneParams &p, const ViewParams &v, const cloud_volu
 template <int CH>
 const void *batch_kernel_ch(int precision, int light_steps, bool fx, int shape);
 // True when a launch can use the FX march: the standard tile sizes, all three
-// tiles present, noise density and six light steps.
+// tiles present, noise density, six light steps and a base tile period of 2^k
+// detail periods (the detail coordinates then follow from the base ones).
 bool fixed_sizes(const SceneParams &p, const cloud_volume *vol);
 
 }  // namespace cloudvol

@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
     march_kernel(const __grid_constant__ SceneParams p, const __grid_constant__ ViewParams v,
                  const T *__restrict__ base, const T *__restrict__ detail,
                  const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
-    __shared__ WarpScratch<CH> scratch[4];
+    __shared__ WarpScratch<CH, FX> scratch[4];
     const unsigned long long n = march_tile<T, LS, SHAPE, FX, CH>(
         p, v, blockIdx.x, blockIdx.y, scratch[threadIdx.x >> 5], base, detail, weather);
     count_lookups(counter, n);
@@ -25,12 +25,12 @@ __global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
 // is found by binary search over the views' first tile indices and staged in
 // shared memory.
 template <typename T, int LS, int SHAPE, bool FX, int CH>
-__global__ void __launch_bounds__(128, BatchBlocks<T, FX>::value)
+__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
     march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
                        int n_views, int total_tiles, unsigned int *__restrict__ work,
                        const T *__restrict__ base, const T *__restrict__ detail,
                        const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
-    __shared__ WarpScratch<CH> scratch[4];
+    __shared__ WarpScratch<CH, FX> scratch[4];
     __shared__ ViewParams sv;
     __shared__ int s_tile, s_view;
     unsigned long long n_look = 0;

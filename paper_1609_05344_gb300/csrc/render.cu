@@ -178,7 +178,7 @@ void set_tuned_config(int precision, int light_steps, int config) {
 bool fixed_sizes(const SceneParams &p, const cloud_volume *vol) {
     return p.light_steps == 6 && !p.constant_mode && vol->detail && vol->weather &&
            p.log2_base == kStdLog2Base && p.log2_detail == kStdLog2Detail &&
-           p.log2_weather == kStdLog2Weather;
+           p.log2_weather == kStdLog2Weather && p.detail_shift >= 0;
 }
 
 int launch_march(const SceneParams &p, const ViewParams &v, const cloud_volume *vol,
