@@ -29,17 +29,32 @@
 
 namespace cloudvol {
 
-// FP32 records at the standard tile sizes: 8 CTAs (64 registers, no spills;
-// 148.8 us at fast-1080p against 154.5 us with 7 and 154.2 us with 9)
+// Records at the standard tile sizes, 8 view steps per warp iteration: 8 CTAs
+// (64 registers, no spills; FP32 148.8 us at fast-1080p against 154.5 us with
+// 7 and 154.2 us with 9; FP16 152.4 us against 153.0 us with 7).  With 16 steps
+// per iteration the per-warp scratch is 1.7x larger and 8 CTAs would leave the
+// L1 28 KB: 7 CTAs for FP32 records and 6 for 16-bit ones (the 64-view batch,
+// BF16: 18.7 ms against 19.5 ms with 8).
 #ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX
 #define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX 8
 #endif
-template <typename T, bool FX>
-struct MarchBlocks { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_16; };
-template <>
-struct MarchBlocks<float, false> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32; };
-template <>
-struct MarchBlocks<float, true> { static constexpr int value = CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX; };
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS_16_FX
+#define CLOUDVOL_MARCH_MIN_BLOCKS_16_FX 8
+#endif
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX16
+#define CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX16 7
+#endif
+#ifndef CLOUDVOL_MARCH_MIN_BLOCKS_16_FX16
+#define CLOUDVOL_MARCH_MIN_BLOCKS_16_FX16 6
+#endif
+template <typename T, bool FX, int CH>
+struct MarchBlocks {
+    static constexpr bool f32 = sizeof(T) == 4;
+    static constexpr int value =
+        !FX ? (f32 ? CLOUDVOL_MARCH_MIN_BLOCKS_F32 : CLOUDVOL_MARCH_MIN_BLOCKS_16)
+        : CH <= 8 ? (f32 ? CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX : CLOUDVOL_MARCH_MIN_BLOCKS_16_FX)
+                  : (f32 ? CLOUDVOL_MARCH_MIN_BLOCKS_F32_FX16 : CLOUDVOL_MARCH_MIN_BLOCKS_16_FX16);
+};
 
 // The standard tile sizes (128^3 base, 32^3 detail, 512^2 weather records) as
 // compile-time constants: with FX the record-index and weight shifts of every
@@ -55,17 +70,24 @@ constexpr int kStdLog2Base = 7, kStdLog2Detail = 5, kStdLog2Weather = 9;
 #define CLOUDVOL_LIGHT_UNROLL_16 2
 #endif
 // View lookups a lane evaluates per round of the shared-out view phase (their
-// record loads can overlap; more of them cost registers).
+// record loads can overlap; more of them cost registers): one for FP32
+// records; for 16-bit records one with 8 view steps per iteration (the
+// registers buy an eighth CTA per SM instead) and two with 16.
 #ifndef CLOUDVOL_VIEW_BATCH_F32
 #define CLOUDVOL_VIEW_BATCH_F32 1
 #endif
 #ifndef CLOUDVOL_VIEW_BATCH_16
-#define CLOUDVOL_VIEW_BATCH_16 2
+#define CLOUDVOL_VIEW_BATCH_16 1
 #endif
-template <typename T>
-struct ViewBatch { static constexpr int value = CLOUDVOL_VIEW_BATCH_16; };
-template <>
-struct ViewBatch<float> { static constexpr int value = CLOUDVOL_VIEW_BATCH_F32; };
+#ifndef CLOUDVOL_VIEW_BATCH_16_CH16
+#define CLOUDVOL_VIEW_BATCH_16_CH16 2
+#endif
+template <typename T, int CH>
+struct ViewBatch {
+    static constexpr int value = sizeof(T) == 4 ? CLOUDVOL_VIEW_BATCH_F32
+                                 : CH <= 8      ? CLOUDVOL_VIEW_BATCH_16
+                                                : CLOUDVOL_VIEW_BATCH_16_CH16;
+};
 template <typename T>
 struct LightUnroll { static constexpr int value = CLOUDVOL_LIGHT_UNROLL_16; };
 template <>
@@ -469,7 +491,7 @@ __device__ __forceinline__ unsigned long long march_tile(
             nq += __popc(m);
         }
         __syncwarp();
-        constexpr int kViewBatch = ViewBatch<T>::value;
+        constexpr int kViewBatch = ViewBatch<T, CH>::value;
         for (unsigned q = lane; q < nq; q += 32 * kViewBatch) {
             // a lane without a further lookup repeats its first (same value, same entry)
             unsigned pr[kViewBatch];

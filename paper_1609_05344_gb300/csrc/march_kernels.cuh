@@ -10,7 +10,7 @@
 namespace cloudvol {
 
 template <typename T, int LS, int SHAPE, bool FX, int CH>
-__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
+__global__ void __launch_bounds__(128, MarchBlocks<T, FX, CH>::value)
     march_kernel(const __grid_constant__ SceneParams p, const __grid_constant__ ViewParams v,
                  const T *__restrict__ base, const T *__restrict__ detail,
                  const T *__restrict__ weather, unsigned long long *__restrict__ counter) {
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
 // is found by binary search over the views' first tile indices and staged in
 // shared memory.
 template <typename T, int LS, int SHAPE, bool FX, int CH>
-__global__ void __launch_bounds__(128, MarchBlocks<T, FX>::value)
+__global__ void __launch_bounds__(128, MarchBlocks<T, FX, CH>::value)
     march_batch_kernel(const __grid_constant__ SceneParams p, const ViewParams *__restrict__ views,
                        int n_views, int total_tiles, unsigned int *__restrict__ work,
                        const T *__restrict__ base, const T *__restrict__ detail,
