@@ -80,6 +80,30 @@ def test_full_volume_jittered_small(api, oracle, frame, integration):
     assert _max_err(got, ref) <= TOL_FP32
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("fp16", TOL_FP16)])
+def test_non_dyadic_detail_period(api, oracle, precision, tol):
+    """The standard tile sizes with a base tile period that is not 2^k detail
+    periods (6400 m / 1000 m): the march then converts the detail coordinates
+    separately (the generic kernel) and the occupancy grid bounds the detail
+    term by the whole detail tile's minimum.  Every pixel against the FP64
+    oracle, and the grid's skips bitwise exact."""
+    desc = I.volume_desc("full", seed=5, detail_period=1000.0)
+    vol = api.Volume(dict(desc, precision=precision))
+    ovol = oracle.Volume(desc)
+    cam = I.orbit_camera(4, 5)
+    w, h = 80, 45
+    got = api.render(vol, cam, I.params(), w, h, 8, 6, jitter_frame=4).cpu().numpy()
+    ref, _ = oracle.render(ovol, cam, I.params(), w, h, 8, 6, jitter_frame=4, nthreads=8)
+    assert _max_err(got, ref) <= tol
+    assert ref[..., 3].max() > 0.1
+    api.set_occupancy(False)
+    try:
+        plain = api.render(vol, cam, I.params(), w, h, 8, 6, jitter_frame=4).cpu().numpy()
+    finally:
+        api.set_occupancy(True)
+    assert np.array_equal(plain, got)
+
+
 def _sampled(api, oracle, wl, cam, frame, n, seed, precision="fp32", steps=None):
     desc = dict(wl.volume, precision=precision)
     vol = api.Volume(desc)
