@@ -343,8 +343,8 @@ __device__ __forceinline__ float step_depth(float absorption, float rho, float D
 //   A  view densities and the early out (the optical depth does not depend on
 //      the lighting): each lane marks which of its steps need a lookup (inside
 //      the layer, occupied macro-cell), the warp shares those lookups out over
-//      all 32 lanes, two per lane at a time, and each lane then walks its own
-//      steps in order for the optical depth and the early out;
+//      all 32 lanes, ViewBatch per lane at a time, and each lane then walks its
+//      own steps in order for the optical depth and the early out;
 //   B  the warp shares out every (step, lane) light march with density > 0
 //      over all 32 lanes, so lanes whose own rays are empty, finished or
 //      outside the layer do useful work;
