@@ -518,7 +518,7 @@ __device__ __forceinline__ unsigned long long march_tile(
         int nA = 0;
         if (alive) {
             float tau_a = tau;
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < CH; ++k) {
                 if (i0 + k >= v.steps) break;
                 const float rho = ((need >> k) & 1u) ? ws.rho[k][lane] : 0.0f;
