@@ -273,7 +273,7 @@ __device__ __forceinline__ float trilinear_at(const float v[8], float fx, float 
 // 1e-5 covers FP32 rounding of the lerps and of the remap.
 template <typename T>
 __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T *__restrict__ detail,
-                                 int log2d, double ratio, float dt_all_lo, float dt_all_hi,
+                                 int log2d, float ratio, float dt_all_lo, float dt_all_hi,
                                  float k0, float wd, uint32_t *__restrict__ occ) {
     const int lo2 = log2b - kOccShift;
     const uint32_t M = 1u << lo2, nd = 1u << log2d;
@@ -295,14 +295,14 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
                         bmax = fmaxf(bmax, h);
                     }
             float dlo = dt_all_lo, dhi = dt_all_hi;
-            if (detail && ratio > 0.0) {
+            if (detail && ratio > 0.0f) {
                 // detail record range along each axis: samples with base texel-centre
                 // coordinate s in [m K, m K + m) have detail coordinate (s + 1/2) ratio - 1/2
                 const uint32_t K[3] = {X, Y, Z};
                 int r0[3], r1[3];
                 for (int a = 0; a < 3; ++a) {
-                    r0[a] = (int)floor(((double)m * K[a] + 0.5) * ratio - 0.5);
-                    r1[a] = (int)floor(((double)m * K[a] + m + 0.5) * ratio - 0.5);
+                    r0[a] = (int)floorf(((float)(m * K[a]) + 0.5f) * ratio - 0.5f);
+                    r1[a] = (int)floorf(((float)(m * K[a] + m) + 0.5f) * ratio - 0.5f);
                 }
                 dlo = INFINITY;
                 dhi = -INFINITY;
@@ -336,7 +336,7 @@ __global__ void occupancy_kernel(const T *__restrict__ base, int log2b, const T 
 // max B - w_d min Dt - c < -1e-5 (room for FP32 rounding).
 template <typename T>
 __global__ void occupancy_half_kernel(const T *__restrict__ base, int log2b,
-                                      const T *__restrict__ detail, int log2d, double ratio,
+                                      const T *__restrict__ detail, int log2d, float ratio,
                                       float dt_all_lo, float dt_all_hi, float k0, float wd,
                                       uint32_t *__restrict__ occ) {
     const int lc = log2b + 1;
@@ -356,19 +356,20 @@ __global__ void occupancy_half_kernel(const T *__restrict__ base, int log2b,
                                                 0.5f * ((K[1] & 1) + ((r >> 1) & 1)),
                                                 0.5f * ((K[2] & 1) + (r & 1))));
             float dlo = dt_all_lo, dhi = dt_all_hi;
-            if (detail && ratio > 0.0) {
+            if (detail && ratio > 0.0f) {
                 // per axis: the cell's detail coordinates [lo, hi) and the points
-                // where Dt can be extreme (lo, the lattice integers inside, hi)
-                double pts[3][6];
+                // where Dt can be extreme (lo, the lattice integers inside, hi);
+                // ratio is a power of two and K < 2^16, so these are exact in FP32
+                float pts[3][6];
                 int np[3];
                 bool ok = true;
                 for (int a = 0; a < 3; ++a) {
-                    const double lo = (0.5 * K[a] + 0.5) * ratio - 0.5;
-                    const double hi = (0.5 * K[a] + 1.0) * ratio - 0.5;
+                    const float lo = (0.5f * (float)K[a] + 0.5f) * ratio - 0.5f;
+                    const float hi = (0.5f * (float)K[a] + 1.0f) * ratio - 0.5f;
                     int n = 0;
                     pts[a][n++] = lo;
-                    for (double q = floor(lo) + 1.0; q < hi && n < 5; q += 1.0) pts[a][n++] = q;
-                    if (floor(lo) + 1.0 + (n - 1) < hi) ok = false;  // more planes than kept
+                    for (float q = floorf(lo) + 1.0f; q < hi && n < 5; q += 1.0f) pts[a][n++] = q;
+                    if (floorf(lo) + 1.0f + (float)(n - 1) < hi) ok = false;  // more planes than kept
                     pts[a][n++] = hi;
                     np[a] = n;
                 }
@@ -378,13 +379,13 @@ __global__ void occupancy_half_kernel(const T *__restrict__ base, int log2b,
                     for (int iz = 0; iz < np[2]; ++iz)
                         for (int iy = 0; iy < np[1]; ++iy)
                             for (int ix = 0; ix < np[0]; ++ix) {
-                                const double sp[3] = {pts[0][ix], pts[1][iy], pts[2][iz]};
+                                const float sp[3] = {pts[0][ix], pts[1][iy], pts[2][iz]};
                                 uint32_t ri[3];
                                 float f[3];
                                 for (int a = 0; a < 3; ++a) {
-                                    const double fl = floor(sp[a]);
-                                    ri[a] = (uint32_t)((long long)fl & (long long)(nd - 1));
-                                    f[a] = (float)(sp[a] - fl);
+                                    const float fl = floorf(sp[a]);
+                                    ri[a] = (uint32_t)((int)fl & (int)(nd - 1));
+                                    f[a] = sp[a] - fl;
                                 }
                                 float dv[8];
                                 record_corners(detail, (ri[2] << (2 * log2d)) | (ri[1] << log2d) | ri[0], dv);
@@ -479,11 +480,11 @@ int build_occupancy(cloud_volume *v, cudaStream_t s) {
     }
     if (kOccShift < 0)
         occupancy_half_kernel<T><<<grid_for(words, 128), 128, 0, s>>>(
-            (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, ratio, range[0],
+            (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, (float)ratio, range[0],
             range[1], k0, (float)wd, v->occ);
     else
         occupancy_kernel<T><<<grid_for(words, 128), 128, 0, s>>>(
-            (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, ratio, range[0],
+            (const T *)v->base, v->log2_base, (const T *)v->detail, v->log2_detail, (float)ratio, range[0],
             range[1], k0, (float)wd, v->occ);
     return check_launch("occupancy_kernel");
 }
