@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256, CLOUDVOL_TAA_MIN_BLOCKS)
 // is tile b of the concatenated views' tile lists; its view is found by
 // binary search over the views' first tiles and its motion constants staged
 // in shared memory.  Each tile is computed exactly as by taa_reproject_kernel.
-struct alignas(64) ResolveView {
+struct alignas(128) ResolveView {  // the tensor map's own alignment
     CUtensorMap map;  // the view's current frame
     MotionParams mp;
     const void *hist;
